@@ -1,0 +1,276 @@
+// C ABI of the batched small-matrix GEMM library (declarations and the
+// argument conventions are in include/sbgemm.h).
+//
+// Each call validates its arguments (dimensions and trans characters of
+// Section 2, leading dimensions of the Section 4 layout), classifies alpha
+// and beta when they are host scalars (the functor choice of Section 5:
+// beta == 0 never reads C; alpha == 0 or k == 0 reduces to C = beta*C),
+// picks a kernel variant from the selection table, and launches.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "sbgemm_launch.cuh"
+#include "sbgemm_shapes.h"
+
+namespace sbg {
+
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+namespace {
+
+int op_code(char t) {
+    switch (t) {
+    case 'n': case 'N': return 0;
+    case 't': case 'T': return 1;
+    case 'c': case 'C': return 2;
+    default: return -1;
+    }
+}
+
+bool is_complex_type(int type) { return type == SBGEMM_TYPE_C || type == SBGEMM_TYPE_Z; }
+
+bool host_scalar_zero(int type, const void* p) {
+    switch (type) {
+    case SBGEMM_TYPE_D: return *static_cast<const double*>(p) == 0.0;
+    case SBGEMM_TYPE_C: { const float* f = static_cast<const float*>(p); return f[0] == 0.f && f[1] == 0.f; }
+    case SBGEMM_TYPE_Z: { const double* d = static_cast<const double*>(p); return d[0] == 0.0 && d[1] == 0.0; }
+    default: return *static_cast<const float*>(p) == 0.f;
+    }
+}
+
+// selection table: (type, m, n, k, ta, tb, beta_zero, size_class) -> variant
+using Key = std::tuple<int, int, int, int, int, int, int, int>;
+std::mutex g_choice_mu;
+std::map<Key, int> g_choice;
+
+int size_class(int batch) {
+    int c = 0;
+    while (batch >= 10 && c < 7) { batch /= 10; ++c; }
+    return c;
+}
+
+int lookup_choice(int type, int m, int n, int k, int ta, int tb, int bz, int sc) {
+    std::lock_guard<std::mutex> lk(g_choice_mu);
+    auto it = g_choice.find(Key(type, m, n, k, ta, tb, bz, sc));
+    return it == g_choice.end() ? -1 : it->second;
+}
+
+int variants_for(int m, int n, int k) {
+    if (m < 1 || n < 1 || k < 1 || m > 16 || n > 16 || k > 16) return 0;
+    return has_specialized(0, m, n, k) ? kNumPipeVariants + 1 : 1;
+}
+
+// Map a public variant index to the internal one (generic kernel index =
+// kNumPipeVariants).
+int internal_variant(int m, int n, int k, int v) {
+    return has_specialized(0, m, n, k) ? v : kNumPipeVariants;
+}
+
+sbgemm_status run_typed(const Req& r) {
+    switch (r.type) {
+    case SBGEMM_TYPE_S: return run_S(r);
+    case SBGEMM_TYPE_D: return run_D(r);
+    case SBGEMM_TYPE_C: return run_C(r);
+    case SBGEMM_TYPE_Z: return run_Z(r);
+    case SBGEMM_TYPE_H: return run_H(r);
+    case SBGEMM_TYPE_B: return run_B(r);
+    default: return SBGEMM_ERR_INVALID_VALUE;
+    }
+}
+
+sbgemm_status scale_typed(const Req& r) {
+    switch (r.type) {
+    case SBGEMM_TYPE_S: return launch_scale<TyS>(r);
+    case SBGEMM_TYPE_D: return launch_scale<TyD>(r);
+    case SBGEMM_TYPE_C: return launch_scale<TyC>(r);
+    case SBGEMM_TYPE_Z: return launch_scale<TyZ>(r);
+    case SBGEMM_TYPE_H: return launch_scale<TyH>(r);
+    case SBGEMM_TYPE_B: return launch_scale<TyB>(r);
+    default: return SBGEMM_ERR_INVALID_VALUE;
+    }
+}
+
+}  // namespace
+
+// Shared by every uniform-layout entry point.  variant < 0: use the table.
+sbgemm_status gemm_uniform(int type, char transa, char transb, int m, int n, int k,
+                           const void* alpha, const void* A, int lda, long long lda2,
+                           const void* B, int ldb, long long ldb2,
+                           const void* beta, void* C, int ldc, long long ldc2, int batch,
+                           int scalar_mode, int variant, cudaStream_t stream)
+{
+    if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
+    int opa = op_code(transa), opb = op_code(transb);
+    if (opa < 0 || opb < 0) return SBGEMM_ERR_INVALID_TRANS;
+    if (m < 0 || n < 0 || k < 0 || m > 16 || n > 16 || k > 16 || batch < 0)
+        return SBGEMM_ERR_INVALID_SIZE;
+    if (scalar_mode != SBGEMM_SCALARS_HOST && scalar_mode != SBGEMM_SCALARS_DEVICE)
+        return SBGEMM_ERR_INVALID_VALUE;
+    const long long ar = opa == 0 ? m : k, ac = opa == 0 ? k : m;
+    const long long br = opb == 0 ? k : n, bc = opb == 0 ? n : k;
+    auto max1 = [](long long v) { return v > 1 ? v : 1LL; };
+    if (lda < max1(ar) || ldb < max1(br) || ldc < max1(m)) return SBGEMM_ERR_INVALID_LD;
+    if (lda2 != 0 && lda2 < (long long)lda * ac) return SBGEMM_ERR_INVALID_LD;
+    if (ldb2 != 0 && ldb2 < (long long)ldb * bc) return SBGEMM_ERR_INVALID_LD;
+    if (lda2 < 0 || ldb2 < 0 || ldc2 < (long long)ldc * n) return SBGEMM_ERR_INVALID_LD;
+    if (batch == 0 || m == 0 || n == 0) return SBGEMM_SUCCESS;   // quick return
+    if (!alpha || !beta || !C) return SBGEMM_ERR_NULL_POINTER;
+
+    Req r;
+    std::memset(&r, 0, sizeof r);
+    r.type = type; r.m = m; r.n = n; r.k = k;
+    const bool cplx = is_complex_type(type);
+    r.ta = opa != 0; r.tb = opb != 0;
+    r.conja = cplx && opa == 2; r.conjb = cplx && opb == 2;
+    r.A = A; r.B = B; r.C = C;
+    r.lda = lda; r.ldb = ldb; r.ldc = ldc;
+    r.lda2 = lda2; r.ldb2 = ldb2; r.ldc2 = ldc2;
+    r.batch = batch;
+    r.scalar_mode = scalar_mode;
+    r.alpha = alpha; r.beta = beta;
+    r.stream = stream;
+    if (scalar_mode == SBGEMM_SCALARS_HOST) {
+        r.alpha_zero = host_scalar_zero(type, alpha);
+        r.beta_zero = host_scalar_zero(type, beta);
+    }
+    if (k == 0 || r.alpha_zero) return scale_typed(r);   // C = beta*C, A and B unread
+    if (!A || !B) return SBGEMM_ERR_NULL_POINTER;
+
+    const int nv = variants_for(m, n, k);
+    if (variant >= 0) {
+        if (variant >= nv) return SBGEMM_ERR_INVALID_VALUE;
+    } else {
+        variant = lookup_choice(type, m, n, k, r.ta, r.tb,
+                                scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
+                                size_class(batch));
+        if (variant < 0 || variant >= nv) variant = 0;
+    }
+    r.variant = internal_variant(m, n, k, variant);
+    return run_typed(r);
+}
+
+}  // namespace sbg
+
+using sbg::gemm_uniform;
+
+extern "C" {
+
+#define SBG_PAPER_ENTRY(L, T, CODE)                                                         \
+    sbgemm_status sbgemm_##L##gemm_multi_uniform(char transa, char transb, int m, int n, int k, \
+        const T* alpha, const T* A, int lda, long long lda2, const T* B, int ldb,           \
+        long long ldb2, const T* beta, T* C, int ldc, long long ldc2, int batchCount) {     \
+        return gemm_uniform(CODE, transa, transb, m, n, k, alpha, A, lda, lda2, B, ldb,     \
+                            ldb2, beta, C, ldc, ldc2, batchCount, SBGEMM_SCALARS_HOST, -1,  \
+                            (cudaStream_t)0);                                               \
+    }                                                                                       \
+    sbgemm_status sbgemm_##L##gemm_multi_uniform_async(char transa, char transb, int m,     \
+        int n, int k, const T* alpha, const T* A, int lda, long long lda2, const T* B,      \
+        int ldb, long long ldb2, const T* beta, T* C, int ldc, long long ldc2,              \
+        int batchCount, int scalar_mode, void* stream) {                                    \
+        return gemm_uniform(CODE, transa, transb, m, n, k, alpha, A, lda, lda2, B, ldb,     \
+                            ldb2, beta, C, ldc, ldc2, batchCount, scalar_mode, -1,          \
+                            (cudaStream_t)stream);                                          \
+    }
+
+SBG_PAPER_ENTRY(S, float, SBGEMM_TYPE_S)
+SBG_PAPER_ENTRY(D, double, SBGEMM_TYPE_D)
+SBG_PAPER_ENTRY(C, sbgemm_c32, SBGEMM_TYPE_C)
+SBG_PAPER_ENTRY(Z, sbgemm_c64, SBGEMM_TYPE_Z)
+#undef SBG_PAPER_ENTRY
+
+sbgemm_status sbgemm_Hgemm_multi_uniform_async(char transa, char transb, int m, int n, int k,
+    const float* alpha, const uint16_t* A, int lda, long long lda2,
+    const uint16_t* B, int ldb, long long ldb2,
+    const float* beta, uint16_t* C, int ldc, long long ldc2, int batchCount,
+    int scalar_mode, void* stream) {
+    return gemm_uniform(SBGEMM_TYPE_H, transa, transb, m, n, k, alpha, A, lda, lda2, B, ldb,
+                        ldb2, beta, C, ldc, ldc2, batchCount, scalar_mode, -1, (cudaStream_t)stream);
+}
+
+sbgemm_status sbgemm_Bgemm_multi_uniform_async(char transa, char transb, int m, int n, int k,
+    const float* alpha, const uint16_t* A, int lda, long long lda2,
+    const uint16_t* B, int ldb, long long ldb2,
+    const float* beta, uint16_t* C, int ldc, long long ldc2, int batchCount,
+    int scalar_mode, void* stream) {
+    return gemm_uniform(SBGEMM_TYPE_B, transa, transb, m, n, k, alpha, A, lda, lda2, B, ldb,
+                        ldb2, beta, C, ldc, ldc2, batchCount, scalar_mode, -1, (cudaStream_t)stream);
+}
+
+int sbgemm_num_variants(int type, int m, int n, int k) {
+    if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return 0;
+    return sbg::variants_for(m, n, k);
+}
+
+const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
+    static const char* names[] = {
+        "pipe tile16K st3 occ-max", "pipe tile8K st4 occ-max", "pipe tile32K st2 occ-max",
+        "pipe tile16K st3 1cta/sm", "pipe tile4K st4 occ-max", "pipe tile24K st3 2cta/sm",
+        "generic thread-per-entry"};
+    const int nv = sbgemm_num_variants(type, m, n, k);
+    if (variant < 0 || variant >= nv) return "invalid";
+    return names[sbg::internal_variant(m, n, k, variant)];
+}
+
+sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char transb,
+    int m, int n, int k, const void* alpha, const void* A, int lda, long long lda2,
+    const void* B, int ldb, long long ldb2, const void* beta, void* C, int ldc,
+    long long ldc2, int batchCount, int scalar_mode, int variant, void* stream) {
+    if (variant < 0) return SBGEMM_ERR_INVALID_VALUE;
+    return gemm_uniform(type, transa, transb, m, n, k, alpha, A, lda, lda2, B, ldb, ldb2,
+                        beta, C, ldc, ldc2, batchCount, scalar_mode, variant, (cudaStream_t)stream);
+}
+
+sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
+                                int beta_zero, int size_class, int variant) {
+    if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
+    const int nv = sbg::variants_for(m, n, k);
+    if (nv == 0 || variant >= nv || size_class < 0 || size_class > 7) return SBGEMM_ERR_INVALID_VALUE;
+    std::lock_guard<std::mutex> lk(sbg::g_choice_mu);
+    sbg::Key key(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
+    if (variant < 0) sbg::g_choice.erase(key);
+    else sbg::g_choice[key] = variant;
+    return SBGEMM_SUCCESS;
+}
+
+int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb, int beta_zero, int size_class) {
+    const int v = sbg::lookup_choice(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
+    return v < 0 ? 0 : v;
+}
+
+void sbgemm_clear_choices(void) {
+    std::lock_guard<std::mutex> lk(sbg::g_choice_mu);
+    sbg::g_choice.clear();
+}
+
+const char* sbgemm_status_string(sbgemm_status s) {
+    switch (s) {
+    case SBGEMM_SUCCESS: return "success";
+    case SBGEMM_ERR_INVALID_TRANS: return "invalid trans character";
+    case SBGEMM_ERR_INVALID_SIZE: return "m, n, k outside 0..16 or negative batch count";
+    case SBGEMM_ERR_INVALID_LD: return "leading dimension below its minimum";
+    case SBGEMM_ERR_NULL_POINTER: return "null pointer";
+    case SBGEMM_ERR_INVALID_VALUE: return "invalid argument";
+    case SBGEMM_ERR_TIMEOUT: return "bounded in-kernel wait expired";
+    case SBGEMM_ERR_NOT_SUPPORTED: return "not supported";
+    case SBGEMM_ERR_CAPACITY: return "request exceeds a fixed capacity";
+    default: return s > 0 ? cudaGetErrorString((cudaError_t)s) : "unknown status";
+    }
+}
+
+int sbgemm_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,468 @@
+// Device code for batched small-matrix GEMM on sm_103a.
+//
+// Operation (arXiv 1304.7053, Section 2, Eq. 1), for every pair p:
+//     C_p <- alpha * op(A_p) * op(B_p) + beta * C_p
+// on the uniform 3-D layout of Section 4: X_p(i, j) = X[i + ldx*j + ldx2*p].
+//
+// Kernel structure (the design is ours; the paper's Kepler kernels are prior
+// art only):
+//   * A persistent grid walks tiles of P consecutive pairs (grid-stride).
+//   * Each tile's A, B (and old C when beta != 0) are staged into shared
+//     memory by a STAGES-deep cp.async pipeline.  When an operand is a flat
+//     stream (minimal leading dimensions, 16-byte aligned), the tile is one
+//     contiguous span copied in coalesced 16-byte chunks; matrices whose
+//     byte size is an even number of 16-byte chunks get a one-chunk pad per
+//     matrix slot so neighbouring matrices start in different bank groups.
+//     Other layouts are gathered element by element (still asynchronous).
+//   * Each thread owns a TM x TN block of one C_p and keeps it in
+//     registers; op() is applied by the index map used to read shared
+//     memory (Section 2), conjugation by a sign on the imaginary part
+//     (Section 5 "conjugate" functor).
+//   * The epilogue is alpha*acc when beta == 0, where C is never read
+//     (Section 5 "axpby_a1b0"), else alpha*acc + beta*C_old (Section 5
+//     "axpby").  Results go to a shared-memory tile and leave in coalesced
+//     16-byte stores.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace sbg {
+
+// ------------------------------------------------------------ scalar types
+
+// Storage type S, arithmetic type A (fp32 for the 16-bit storage types).
+struct TyS { using S = float;   using A = float;   using R = float;  static constexpr bool cplx = false; static constexpr int code = 0; };
+struct TyD { using S = double;  using A = double;  using R = double; static constexpr bool cplx = false; static constexpr int code = 1; };
+struct TyC { using S = float2;  using A = float2;  using R = float;  static constexpr bool cplx = true;  static constexpr int code = 2; };
+struct TyZ { using S = double2; using A = double2; using R = double; static constexpr bool cplx = true;  static constexpr int code = 3; };
+struct TyH { using S = __half;        using A = float; using R = float; static constexpr bool cplx = false; static constexpr int code = 4; };
+struct TyB { using S = __nv_bfloat16; using A = float; using R = float; static constexpr bool cplx = false; static constexpr int code = 5; };
+
+__device__ __forceinline__ float  to_a(float x)  { return x; }
+__device__ __forceinline__ double to_a(double x) { return x; }
+__device__ __forceinline__ float2 to_a(float2 x) { return x; }
+__device__ __forceinline__ double2 to_a(double2 x) { return x; }
+__device__ __forceinline__ float  to_a(__half x) { return __half2float(x); }
+__device__ __forceinline__ float  to_a(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class Ty> __device__ __forceinline__ typename Ty::S to_s(typename Ty::A x);
+template <> __device__ __forceinline__ float   to_s<TyS>(float x)   { return x; }
+template <> __device__ __forceinline__ double  to_s<TyD>(double x)  { return x; }
+template <> __device__ __forceinline__ float2  to_s<TyC>(float2 x)  { return x; }
+template <> __device__ __forceinline__ double2 to_s<TyZ>(double2 x) { return x; }
+template <> __device__ __forceinline__ __half  to_s<TyH>(float x)   { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_s<TyB>(float x) { return __float2bfloat16_rn(x); }
+
+template <class A> __device__ __forceinline__ A zero_a();
+template <> __device__ __forceinline__ float   zero_a<float>()   { return 0.f; }
+template <> __device__ __forceinline__ double  zero_a<double>()  { return 0.0; }
+template <> __device__ __forceinline__ float2  zero_a<float2>()  { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 zero_a<double2>() { return make_double2(0.0, 0.0); }
+
+// acc += a * b  (fused; complex uses the 4-multiply form, no 3M method,
+// matching the flop convention of Section 7)
+__device__ __forceinline__ void mac(float& c, float a, float b)   { c = fmaf(a, b, c); }
+__device__ __forceinline__ void mac(double& c, double a, double b) { c = fma(a, b, c); }
+__device__ __forceinline__ void mac(float2& c, float2 a, float2 b) {
+    c.x = fmaf(a.x, b.x, c.x); c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y); c.y = fmaf(a.y, b.x, c.y);
+}
+__device__ __forceinline__ void mac(double2& c, double2 a, double2 b) {
+    c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+}
+
+// imaginary-part sign for conjugation (identity for real types)
+__device__ __forceinline__ float   conj_s(float a, float)     { return a; }
+__device__ __forceinline__ double  conj_s(double a, double)   { return a; }
+__device__ __forceinline__ float2  conj_s(float2 a, float s)  { return make_float2(a.x, a.y * s); }
+__device__ __forceinline__ double2 conj_s(double2 a, double s){ return make_double2(a.x, a.y * s); }
+
+// alpha * x
+__device__ __forceinline__ float   mul(float a, float x)     { return a * x; }
+__device__ __forceinline__ double  mul(double a, double x)   { return a * x; }
+__device__ __forceinline__ float2  mul(float2 a, float2 x)   { return make_float2(fmaf(a.x, x.x, -a.y * x.y), fmaf(a.x, x.y, a.y * x.x)); }
+__device__ __forceinline__ double2 mul(double2 a, double2 x) { return make_double2(fma(a.x, x.x, -a.y * x.y), fma(a.x, x.y, a.y * x.x)); }
+// v + b * c
+__device__ __forceinline__ float   axpy(float b, float c, float v)       { return fmaf(b, c, v); }
+__device__ __forceinline__ double  axpy(double b, double c, double v)    { return fma(b, c, v); }
+__device__ __forceinline__ float2  axpy(float2 b, float2 c, float2 v) {
+    v.x = fmaf(b.x, c.x, v.x); v.x = fmaf(-b.y, c.y, v.x);
+    v.y = fmaf(b.x, c.y, v.y); v.y = fmaf(b.y, c.x, v.y);
+    return v;
+}
+__device__ __forceinline__ double2 axpy(double2 b, double2 c, double2 v) {
+    v.x = fma(b.x, c.x, v.x); v.x = fma(-b.y, c.y, v.x);
+    v.y = fma(b.x, c.y, v.y); v.y = fma(b.y, c.x, v.y);
+    return v;
+}
+__device__ __forceinline__ bool is_zero(float a)   { return a == 0.f; }
+__device__ __forceinline__ bool is_zero(double a)  { return a == 0.0; }
+__device__ __forceinline__ bool is_zero(float2 a)  { return a.x == 0.f && a.y == 0.f; }
+__device__ __forceinline__ bool is_zero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+__device__ __forceinline__ bool is_one(float a)    { return a == 1.f; }
+__device__ __forceinline__ bool is_one(double a)   { return a == 1.0; }
+__device__ __forceinline__ bool is_one(float2 a)   { return a.x == 1.f && a.y == 0.f; }
+__device__ __forceinline__ bool is_one(double2 a)  { return a.x == 1.0 && a.y == 0.0; }
+
+// ------------------------------------------------------------ async copies
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// 16-byte global -> shared copy; bytes beyond src_bytes are zero-filled and
+// not read from global memory.
+__device__ __forceinline__ void cp_async16(void* s, const void* g, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
+                 :: "r"(smem_u32(s)), "l"(g), "r"(src_bytes) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* s, const void* g) {
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n"
+                 :: "r"(smem_u32(s)), "l"(g), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_dyn(int pending) {
+    // pending = number of most recent groups allowed to stay in flight
+    if (pending <= 0)      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else if (pending == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    else                   asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+}
+
+// ------------------------------------------------------------ launch args
+
+template <class Ty>
+struct Args {
+    using S = typename Ty::S;
+    using A = typename Ty::A;
+    const S* A_; const S* B_; S* C_;
+    long long lda2, ldb2, ldc2;
+    int lda, ldb, ldc;
+    int batch;
+    A alpha, beta;               // host scalars (used when the pointers are null)
+    const A* alpha_ptr;          // device scalars (SBGEMM_SCALARS_DEVICE)
+    const A* beta_ptr;
+    typename Ty::R conja, conjb; // +1 or -1: sign applied to imaginary parts
+    int flat;                    // bit 0: A flat, bit 1: B flat, bit 2: C flat
+    int beta_zero;               // host mode: beta == 0 known on the host
+    int alpha_zero;              // host mode: alpha == 0 known on the host
+    int P;                       // pairs per tile
+    int stages;                  // pipeline depth (2..4)
+};
+
+// Pad a matrix slot by one 16-byte chunk when its byte size is an even number
+// of chunks, so consecutive matrices begin in different shared-memory bank
+// groups.  Odd-chunk and non-chunk-multiple sizes stay unpadded.
+__host__ __device__ constexpr int padded_elems(int elems, int es) {
+    return ((elems * es) % 16 == 0 && ((elems * es) / 16) % 2 == 0) ? elems + 16 / es : elems;
+}
+
+// Largest vector (elements, at most 16 bytes) dividing a, b and c.
+__host__ __device__ constexpr int pick_vec(int es, int a, int b, int c) {
+    for (int v = 16 / es; v >= 1; v /= 2)
+        if (v * es <= 16 && a % v == 0 && b % v == 0 && c % v == 0) return v;
+    return 1;
+}
+
+// Compile-time kernel configuration.  TM x TN: the block of C one thread
+// owns; SI / SJ: rows / columns assigned to threads strided (i = ti + TI*r)
+// instead of in contiguous blocks (i = ti*TM + r); NT: threads per block.
+// The tile of each (type, shape, op) comes from the cost model in
+// gen_tiles.py (tile_table.h); the vector widths below follow the same rules.
+template <class Ty_, int M_, int N_, int K_, bool TA_, bool TB_, int TM_, int TN_,
+          bool SI_, bool SJ_, int NT_>
+struct Cfg {
+    using Ty = Ty_;
+    using S = typename Ty::S;
+    using A = typename Ty::A;
+    using R = typename Ty::R;
+    static constexpr int M = M_, N = N_, K = K_, TM = TM_, TN = TN_, NT = NT_;
+    static constexpr bool TA = TA_, TB = TB_, SI = SI_, SJ = SJ_;
+    static constexpr int TI = (M + TM - 1) / TM, TJ = (N + TN - 1) / TN, TPM = TI * TJ;
+    static constexpr bool RAG_I = TI * TM != M, RAG_J = TJ * TN != N;
+    static constexpr int MPR = NT / TPM;   // matrices per compute round
+    static constexpr int ES = sizeof(S);
+    static constexpr int SA = M * K, SB = K * N, SC = M * N;
+    static constexpr int SA_P = padded_elems(SA, ES);
+    static constexpr int SB_P = padded_elems(SB, ES);
+    static constexpr int SC_P = padded_elems(SC, ES);
+    static constexpr int RA = TA ? K : M;  // rows of stored A
+    static constexpr int RB = TB ? N : K;  // rows of stored B
+    // l-chunk: vectors along l for operands stored contiguous in l
+    static constexpr int VL = (TA || !TB) ? pick_vec(ES, K, TA ? SA_P : K, !TB ? SB_P : K) : 1;
+    // vectors along rows of A (stored m x k) / columns of B (stored n x k)
+    static constexpr int VI = (!TA && !SI && !RAG_I) ? pick_vec(ES, TM, M, SA_P) : 1;
+    static constexpr int VJ = (TB && !SJ && !RAG_J) ? pick_vec(ES, TN, N, SB_P) : 1;
+    // direct store of contiguous row blocks of C (0: through a shared tile)
+    static constexpr int VS = (SI || RAG_I) ? 0
+        : (16 / ES >= 1 && TM % (16 / ES) == 0 && M % (16 / ES) == 0 && SC % (16 / ES) == 0) ? 16 / ES
+        : (8 / ES >= 1 && TM % (8 / ES) == 0 && M % (8 / ES) == 0 && SC % (8 / ES) == 0) ? 8 / ES : 0;
+    static_assert(MPR >= 1, "threads per matrix exceeds block size");
+    static_assert(K % VL == 0, "l-chunk must divide k");
+};
+
+// ------------------------------------------------------------ staging
+
+// Stage `cnt` consecutive matrices of one operand (first pair index `p0`)
+// into a shared-memory slot array of stride SP elements.
+template <class S, int SE, int SP, int ROWS, int NT>
+__device__ __forceinline__ void stage_operand(S* sdst, const S* g, long long ld2, int ld,
+                                              long long p0, int cnt, bool flat)
+{
+    constexpr int ES = sizeof(S);
+    const int tid = threadIdx.x;
+    if (flat) {
+        // contiguous span of cnt*SE elements starting 16-byte aligned
+        const char* src = reinterpret_cast<const char*>(g + p0 * (long long)SE);
+        char* dst = reinterpret_cast<char*>(sdst);
+        const int nbytes = cnt * SE * ES;
+        const int nchunks = (nbytes + 15) >> 4;
+        for (int c = tid; c < nchunks; c += NT) {
+            const int b = c << 4;
+            int d = b;
+            if (SP != SE) {              // padded slots: chunks never straddle matrices
+                const int q = b / (SE * ES);
+                d = b + q * (SP - SE) * ES;
+            }
+            const int rem = nbytes - b;
+            cp_async16(dst + d, src + b, rem < 16 ? rem : 16);
+        }
+    } else {
+        const int n = cnt * SE;
+        for (int e = tid; e < n; e += NT) {
+            const int q = e / SE;
+            const int r = e - q * SE;
+            const int row = r % ROWS, col = r / ROWS;
+            const S* src = g + (p0 + q) * ld2 + row + (long long)col * ld;
+            S* dst = sdst + q * SP + r;
+            if constexpr (ES == 4 || ES == 8 || ES == 16) cp_async_elem<ES>(dst, src);
+            else *dst = *src;     // 16-bit storage: plain load
+        }
+    }
+}
+
+// Write `cnt` result matrices from shared memory (stride SP) to global C.
+template <class S, int SE, int SP, int ROWS, int NT>
+__device__ __forceinline__ void store_operand(S* g, const S* ssrc, long long ld2, int ld,
+                                              long long p0, int cnt, bool flat)
+{
+    constexpr int ES = sizeof(S);
+    const int tid = threadIdx.x;
+    if (flat) {
+        char* dst = reinterpret_cast<char*>(g + p0 * (long long)SE);
+        const char* src = reinterpret_cast<const char*>(ssrc);
+        const int nbytes = cnt * SE * ES;
+        const int nfull = nbytes >> 4;
+        for (int c = tid; c < nfull; c += NT) {
+            const int b = c << 4;
+            int d = b;
+            if (SP != SE) {
+                const int q = b / (SE * ES);
+                d = b + q * (SP - SE) * ES;
+            }
+            *reinterpret_cast<uint4*>(dst + b) = *reinterpret_cast<const uint4*>(src + d);
+        }
+        // ragged tail (< 16 bytes): element stores; slots are unpadded here
+        // because a padded slot size is a multiple of 16 bytes
+        const int e0 = (nfull << 4) / ES;
+        const int e1 = nbytes / ES;
+        for (int e = e0 + tid; e < e1; e += NT) {
+            const int q = e / SE;
+            const int r = e - q * SE;
+            reinterpret_cast<S*>(dst)[e] = ssrc[q * SP + r];
+        }
+    } else {
+        const int n = cnt * SE;
+        for (int e = tid; e < n; e += NT) {
+            const int q = e / SE;
+            const int r = e - q * SE;
+            const int row = r % ROWS, col = r / ROWS;
+            g[(p0 + q) * ld2 + row + (long long)col * ld] = ssrc[q * SP + r];
+        }
+    }
+}
+
+// ------------------------------------------------------------ compute
+
+// V consecutive storage elements from 16/8/4-byte aligned shared memory in
+// one vector load, converted to the arithmetic type.
+template <int V, class S, class A>
+__device__ __forceinline__ void ldvec(const S* p, A* out) {
+    constexpr int BYTES = V * (int)sizeof(S);
+    if constexpr (V > 1 && BYTES == 16) {
+        union { uint4 u; S e[V]; } x;
+        x.u = *reinterpret_cast<const uint4*>(p);
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = to_a(x.e[v]);
+    } else if constexpr (V > 1 && BYTES == 8) {
+        union { uint2 u; S e[V]; } x;
+        x.u = *reinterpret_cast<const uint2*>(p);
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = to_a(x.e[v]);
+    } else if constexpr (V > 1 && BYTES == 4) {
+        union { uint32_t u; S e[V]; } x;
+        x.u = *reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = to_a(x.e[v]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = to_a(p[v]);
+    }
+}
+
+// V consecutive storage elements to 16/8/4-byte aligned memory in one store.
+template <int V, class S>
+__device__ __forceinline__ void stvec(S* p, const S* in) {
+    constexpr int BYTES = V * (int)sizeof(S);
+    if constexpr (V > 1 && BYTES == 16) {
+        union { uint4 u; S e[V]; } x;
+#pragma unroll
+        for (int v = 0; v < V; ++v) x.e[v] = in[v];
+        *reinterpret_cast<uint4*>(p) = x.u;
+    } else if constexpr (V > 1 && BYTES == 8) {
+        union { uint2 u; S e[V]; } x;
+#pragma unroll
+        for (int v = 0; v < V; ++v) x.e[v] = in[v];
+        *reinterpret_cast<uint2*>(p) = x.u;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = in[v];
+    }
+}
+
+// One thread: its TM x TN block (ti, tj) of matrix q of the staged tile.
+// op(A)(i, l) = TA ? A[l + K i] : A[i + M l];  op(B)(l, j) = TB ? B[j + N l] : B[l + K j]
+// (Section 2 op, Section 4 layout with minimal leading dimensions).
+// direct: write C straight to gC (matrix q at gC + q*SC) with vector stores,
+// else to the shared tile sOut.
+template <class Cf>
+__device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__ sA,
+                                              const typename Cf::S* __restrict__ sB,
+                                              const typename Cf::S* __restrict__ sCold,
+                                              typename Cf::S* __restrict__ sOut,
+                                              typename Cf::S* __restrict__ gC, bool direct,
+                                              int q, int ti, int tj,
+                                              typename Cf::A alpha, typename Cf::A beta,
+                                              bool beta_zero, bool alpha_one, bool skip_ab,
+                                              typename Cf::R conja, typename Cf::R conjb)
+{
+    using S = typename Cf::S;
+    using A = typename Cf::A;
+    constexpr int M = Cf::M, N = Cf::N, K = Cf::K, TM = Cf::TM, TN = Cf::TN;
+    constexpr int TI = Cf::TI, TJ = Cf::TJ, VL = Cf::VL, VI = Cf::VI, VJ = Cf::VJ;
+    const S* a = sA + q * Cf::SA_P;
+    const S* b = sB + q * Cf::SB_P;
+
+    int ri[TM], cj[TN];   // clamped row / column of each block entry
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+        const int i = Cf::SI ? ti + TI * r : ti * TM + r;
+        ri[r] = i < M ? i : M - 1;
+    }
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+        const int j = Cf::SJ ? tj + TJ * c : tj * TN + c;
+        cj[c] = j < N ? j : N - 1;
+    }
+
+    A acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = zero_a<A>();
+
+    if (!skip_ab) {
+#pragma unroll
+        for (int l0 = 0; l0 < K; l0 += VL) {
+            A av[TM][VL], bv[TN][VL];
+            if constexpr (Cf::TA) {
+#pragma unroll
+                for (int r = 0; r < TM; ++r) ldvec<VL>(a + K * ri[r] + l0, av[r]);
+            } else {
+#pragma unroll
+                for (int dl = 0; dl < VL; ++dl)
+#pragma unroll
+                    for (int rg = 0; rg < TM; rg += VI) {
+                        A t[VI];
+                        ldvec<VI>(a + ri[rg] + M * (l0 + dl), t);
+#pragma unroll
+                        for (int v = 0; v < VI; ++v) av[rg + v][dl] = t[v];
+                    }
+            }
+            if constexpr (!Cf::TB) {
+#pragma unroll
+                for (int c = 0; c < TN; ++c) ldvec<VL>(b + K * cj[c] + l0, bv[c]);
+            } else {
+#pragma unroll
+                for (int dl = 0; dl < VL; ++dl)
+#pragma unroll
+                    for (int cg = 0; cg < TN; cg += VJ) {
+                        A t[VJ];
+                        ldvec<VJ>(b + cj[cg] + N * (l0 + dl), t);
+#pragma unroll
+                        for (int v = 0; v < VJ; ++v) bv[cg + v][dl] = t[v];
+                    }
+            }
+#pragma unroll
+            for (int dl = 0; dl < VL; ++dl) {
+#pragma unroll
+                for (int r = 0; r < TM; ++r) av[r][dl] = conj_s(av[r][dl], conja);
+#pragma unroll
+                for (int c = 0; c < TN; ++c) bv[c][dl] = conj_s(bv[c][dl], conjb);
+#pragma unroll
+                for (int r = 0; r < TM; ++r)
+#pragma unroll
+                    for (int c = 0; c < TN; ++c) mac(acc[r][c], av[r][dl], bv[c][dl]);
+            }
+        }
+    }
+
+    // epilogue: alpha*acc, plus beta*C_old unless beta == 0 (C then unread)
+    auto value = [&](int r, int c, A cold) -> S {
+        A v = alpha_one ? acc[r][c] : mul(alpha, acc[r][c]);
+        if (skip_ab) v = zero_a<A>();
+        if (!beta_zero) v = axpy(beta, cold, v);
+        return to_s<typename Cf::Ty>(v);
+    };
+    const S* co = sCold + q * Cf::SC_P;
+    if constexpr (Cf::VS > 0) {
+        if (direct) {
+            constexpr int VS = Cf::VS;
+            S* g = gC + (long long)q * Cf::SC;
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int j = Cf::SJ ? tj + TJ * c : tj * TN + c;
+                if (Cf::RAG_J && j >= N) continue;
+#pragma unroll
+                for (int rg = 0; rg < TM; rg += VS) {
+                    const int i0 = ti * TM + rg;
+                    A cold[VS];
+                    if (!beta_zero) ldvec<VS>(co + i0 + M * j, cold);
+                    S out[VS];
+#pragma unroll
+                    for (int v = 0; v < VS; ++v) out[v] = value(rg + v, c, beta_zero ? zero_a<A>() : cold[v]);
+                    stvec<VS>(g + i0 + M * j, out);
+                }
+            }
+            return;
+        }
+    }
+    S* o = sOut + q * Cf::SC_P;
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+        const int i = Cf::SI ? ti + TI * r : ti * TM + r;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int j = Cf::SJ ? tj + TJ * c : tj * TN + c;
+            if ((Cf::RAG_I && i >= M) || (Cf::RAG_J && j >= N)) continue;
+            o[i + M * j] = value(r, c, beta_zero ? zero_a<A>() : to_a(co[i + M * j]));
+        }
+    }
+}
+
+}  // namespace sbg

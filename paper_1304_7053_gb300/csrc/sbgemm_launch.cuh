@@ -1,0 +1,403 @@
+// Kernels and host-side launchers for the fixed-size uniform-layout path.
+#pragma once
+
+#include "sbgemm_device.cuh"
+#include "tile_table.h"
+#include "../../include/sbgemm.h"
+
+namespace sbg {
+
+// Host request after argument checks (one per call).
+struct Req {
+    int type;
+    int m, n, k;
+    int ta, tb;            // stored-transposed flags (op = T or C)
+    int conja, conjb;      // conjugation flags (complex types, op = C)
+    const void* A; const void* B; void* C;
+    int lda, ldb, ldc;
+    long long lda2, ldb2, ldc2;
+    int batch;
+    int scalar_mode;
+    const void* alpha;     // host or device pointer to one scalar
+    const void* beta;
+    int beta_zero;         // host scalars only
+    int alpha_zero;
+    int variant;
+    cudaStream_t stream;
+};
+
+// Run-time launch options that do not change the kernel binary.
+struct LaunchOpts {
+    int tile_bytes;    // target staged input bytes per tile
+    int stages;        // pipeline depth, 2..4
+    int ctas_per_sm;   // 0 = as many as fit
+};
+
+// The variant table for the pipelined kernel; the last variant of every
+// shape is the generic runtime-size kernel (one thread per C entry, the
+// mapping of the paper's first method in Section 6).
+constexpr int kNumPipeVariants = 6;
+inline LaunchOpts pipe_variant(int v) {
+    switch (v) {
+    case 1:  return {8192, 4, 0};
+    case 2:  return {32768, 2, 0};
+    case 3:  return {16384, 3, 1};
+    case 4:  return {4096, 4, 0};
+    case 5:  return {24576, 3, 2};
+    default: return {16384, 3, 0};
+    }
+}
+
+int num_sms();  // cached device attribute (api.cu)
+
+template <class Ty>
+inline void fill_args(Args<Ty>& a, const Req& r) {
+    using S = typename Ty::S;
+    using A = typename Ty::A;
+    a.A_ = static_cast<const S*>(r.A);
+    a.B_ = static_cast<const S*>(r.B);
+    a.C_ = static_cast<S*>(r.C);
+    a.lda = r.lda; a.ldb = r.ldb; a.ldc = r.ldc;
+    a.lda2 = r.lda2; a.ldb2 = r.ldb2; a.ldc2 = r.ldc2;
+    a.batch = r.batch;
+    if (r.scalar_mode == SBGEMM_SCALARS_DEVICE) {
+        a.alpha_ptr = static_cast<const A*>(r.alpha);
+        a.beta_ptr = static_cast<const A*>(r.beta);
+        a.alpha = A(); a.beta = A();
+        a.beta_zero = 0; a.alpha_zero = 0;
+    } else {
+        a.alpha_ptr = nullptr; a.beta_ptr = nullptr;
+        a.alpha = *static_cast<const A*>(r.alpha);
+        a.beta = *static_cast<const A*>(r.beta);
+        a.beta_zero = r.beta_zero; a.alpha_zero = r.alpha_zero;
+    }
+    a.conja = r.conja ? typename Ty::R(-1) : typename Ty::R(1);
+    a.conjb = r.conjb ? typename Ty::R(-1) : typename Ty::R(1);
+}
+
+// ------------------------------------------------------------ pipelined kernel
+
+template <class Cf>
+__global__ void __launch_bounds__(Cf::NT)
+pipe_kernel(Args<typename Cf::Ty> g)
+{
+    using S = typename Cf::S;
+    using A = typename Cf::A;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    A alpha = g.alpha, beta = g.beta;
+    bool beta_zero = g.beta_zero != 0, alpha_zero = g.alpha_zero != 0;
+    const bool has_cold = !beta_zero;          // smem layout fixed by the host
+    if (g.alpha_ptr) { alpha = *g.alpha_ptr; alpha_zero = is_zero(alpha); }
+    if (g.beta_ptr)  { beta = *g.beta_ptr;   beta_zero = is_zero(beta); }
+    const bool alpha_one = is_one(alpha);
+    const bool skip_ab = alpha_zero;
+
+    const int P = g.P;
+    const int stages = g.stages;
+    const int stage_elems = P * (Cf::SA_P + Cf::SB_P + (has_cold ? Cf::SC_P : 0));
+    S* stage_base = reinterpret_cast<S*>(smem_raw);
+    S* sOut = stage_base + stages * stage_elems;    // unused when C is stored directly
+
+    const long long batch = g.batch;
+    const int ntiles = (int)((batch + P - 1) / P);
+    const bool fa = g.flat & 1, fb = g.flat & 2, fc = g.flat & 4;
+    const bool direct = (Cf::VS > 0) && fc;
+
+    auto issue = [&](int t, int s) {
+        S* st = stage_base + s * stage_elems;
+        const long long p0 = (long long)t * P;
+        const int cnt = (int)min((long long)P, batch - p0);
+        if (!skip_ab) {
+            stage_operand<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.A_, g.lda2, g.lda, p0, cnt, fa);
+            stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + P * Cf::SA_P, g.B_, g.ldb2, g.ldb, p0, cnt, fb);
+        }
+        if (!beta_zero)
+            stage_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + P * (Cf::SA_P + Cf::SB_P), g.C_,
+                                                              g.ldc2, g.ldc, p0, cnt, fc);
+    };
+
+    for (int s = 0; s < stages - 1; ++s) {
+        const int t = blockIdx.x + s * gridDim.x;
+        if (t < ntiles) issue(t, s);
+        cp_async_commit();
+    }
+
+    const int tid = threadIdx.x;
+    const int ql = tid / Cf::TPM;
+    const int u = tid - ql * Cf::TPM;
+    const int ti = u % Cf::TI, tj = u / Cf::TI;
+    const bool active = ql < Cf::MPR;
+
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int tn = t + (stages - 1) * gridDim.x;
+        if (tn < ntiles) issue(tn, (it + stages - 1) % stages);
+        cp_async_commit();
+        cp_async_wait_dyn(stages - 1);
+        __syncthreads();
+
+        const S* st = stage_base + (it % stages) * stage_elems;
+        const long long p0 = (long long)t * P;
+        const int cnt = (int)min((long long)P, batch - p0);
+        S* gC = g.C_ + p0 * Cf::SC;
+        if (active) {
+            for (int q = ql; q < cnt; q += Cf::MPR)
+                compute_block<Cf>(st, st + P * Cf::SA_P, st + P * (Cf::SA_P + Cf::SB_P), sOut,
+                                  gC, direct, q, ti, tj, alpha, beta, beta_zero, alpha_one,
+                                  skip_ab, g.conja, g.conjb);
+        }
+        // every thread is done reading this stage before it is refilled
+        __syncthreads();
+        if (!direct)
+            store_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.C_, sOut, g.ldc2, g.ldc, p0, cnt, fc);
+    }
+    cp_async_wait_dyn(0);
+}
+
+// ------------------------------------------------------------ host launcher
+
+inline int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
+inline int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
+
+// Tile geometry.  P (pairs per tile) is a whole number of compute rounds
+// (MPR pairs each) near the byte target, a multiple of every operand's
+// 16-byte quantum (so every tile of a flat stream starts 16-byte aligned),
+// within the shared-memory budget, and small enough that the grid has work
+// for every SM when the batch is short.
+struct Geom { int P; size_t smem; };
+
+template <class Cf>
+inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool direct) {
+    constexpr int ES = Cf::ES;
+    int quantum = 1;
+    quantum = lcm_i(quantum, 16 / gcd_i(Cf::SA * ES, 16));
+    quantum = lcm_i(quantum, 16 / gcd_i(Cf::SB * ES, 16));
+    quantum = lcm_i(quantum, 16 / gcd_i(Cf::SC * ES, 16));
+    const size_t in_bpp = (size_t)(Cf::SA_P + Cf::SB_P + (has_cold ? Cf::SC_P : 0)) * ES;
+    const size_t out_bpp = direct ? 0 : (size_t)Cf::SC_P * ES;
+    const size_t per_pair = in_bpp * o.stages + out_bpp;
+    const size_t cap = 200 * 1024;
+    auto round_up = [&](int p) { return (p + quantum - 1) / quantum * quantum; };
+    int R = (int)(o.tile_bytes / ((size_t)Cf::MPR * in_bpp));
+    if (R < 1) R = 1;
+    int P = round_up(Cf::MPR * R);
+    while (P > quantum && (size_t)P * per_pair > cap) {
+        if (R > 1) { --R; P = round_up(Cf::MPR * R); }
+        else P = (P - 1) / quantum * quantum;
+    }
+    if (P < quantum) P = quantum;
+    // fill the GPU: at least two tiles per resident block when possible
+    int per_sm = (int)((227 * 1024) / ((size_t)P * per_pair + 1024));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2048 / Cf::NT) per_sm = 2048 / Cf::NT;
+    if (o.ctas_per_sm > 0 && per_sm > o.ctas_per_sm) per_sm = o.ctas_per_sm;
+    const long long want_tiles = 2LL * num_sms() * per_sm;
+    if ((batch + P - 1) / P < want_tiles) {
+        long long p2 = (batch + want_tiles - 1) / want_tiles;
+        int pn = round_up((int)(p2 < 1 ? 1 : p2));
+        if (pn < P) P = pn;
+    }
+    return Geom{P, (size_t)P * per_pair};
+}
+
+template <class Cf>
+sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
+    using Ty = typename Cf::Ty;
+    Args<Ty> a;
+    fill_args(a, r);
+    const bool has_cold = !a.beta_zero;
+    // flat-stream test per operand: minimal leading dimensions and 16-byte alignment
+    auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    int flat = 0;
+    if (r.lda == Cf::RA && r.lda2 == (long long)Cf::SA && aligned(r.A)) flat |= 1;
+    if (r.ldb == Cf::RB && r.ldb2 == (long long)Cf::SB && aligned(r.B)) flat |= 2;
+    if (r.ldc == Cf::M && r.ldc2 == (long long)Cf::SC && aligned(r.C)) flat |= 4;
+    a.flat = flat;
+    const bool direct = Cf::VS > 0 && (flat & 4);
+    const Geom gm = tile_geom<Cf>(r.batch, o, has_cold, direct);
+    a.P = gm.P;
+    a.stages = o.stages;
+    auto kern = pipe_kernel<Cf>;
+    static bool attr_set = false;   // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return (sbgemm_status)e;
+        attr_set = true;
+    }
+    // occupancy per dynamic shared-memory size, cached per instantiation
+    // (the query costs microseconds of host time on every call otherwise)
+    static thread_local size_t occ_smem = ~(size_t)0;
+    static thread_local int occ_val = 0;
+    static thread_local int occ_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = 0;
+    if (occ_smem == gm.smem && occ_dev == dev) {
+        per_sm = occ_val;
+    } else {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cf::NT, gm.smem);
+        if (e != cudaSuccess) return (sbgemm_status)e;
+        occ_smem = gm.smem; occ_val = per_sm; occ_dev = dev;
+    }
+    if (per_sm < 1) return SBGEMM_ERR_NOT_SUPPORTED;
+    if (o.ctas_per_sm > 0 && per_sm > o.ctas_per_sm) per_sm = o.ctas_per_sm;
+    const long long ntiles = ((long long)r.batch + gm.P - 1) / gm.P;
+    long long grid = (long long)num_sms() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, Cf::NT, gm.smem, r.stream>>>(a);
+    return (sbgemm_status)cudaGetLastError();
+}
+
+// ------------------------------------------------------------ generic kernel
+
+// Any (m, n, k) <= 16 and any op: one thread per entry of C (the mapping of
+// the paper's first method, Section 6), run-time sizes, element gathers.
+template <class Ty>
+__global__ void __launch_bounds__(256)
+generic_kernel(Args<Ty> g, int m, int n, int k, int ta, int tb)
+{
+    using S = typename Ty::S;
+    using A = typename Ty::A;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    A alpha = g.alpha, beta = g.beta;
+    bool beta_zero = g.beta_zero != 0, alpha_zero = g.alpha_zero != 0;
+    if (g.alpha_ptr) { alpha = *g.alpha_ptr; alpha_zero = is_zero(alpha); }
+    if (g.beta_ptr)  { beta = *g.beta_ptr;   beta_zero = is_zero(beta); }
+    const int P = g.P;
+    const int sa = m * k, sb = k * n, sc = m * n;
+    const int ra = ta ? k : m, rb = tb ? n : k;
+    S* sA = reinterpret_cast<S*>(smem_raw);
+    S* sB = sA + P * sa;
+    S* sC = sB + P * sb;
+    const long long batch = g.batch;
+    const int ntiles = (int)((batch + P - 1) / P);
+    const int tid = threadIdx.x;
+    const int mpr = blockDim.x / sc;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long p0 = (long long)t * P;
+        const int cnt = (int)min((long long)P, batch - p0);
+        if (!alpha_zero) {
+            for (int e = tid; e < cnt * sa; e += blockDim.x) {
+                const int q = e / sa, r = e - q * sa;
+                sA[e] = g.A_[(p0 + q) * g.lda2 + r % ra + (long long)(r / ra) * g.lda];
+            }
+            for (int e = tid; e < cnt * sb; e += blockDim.x) {
+                const int q = e / sb, r = e - q * sb;
+                sB[e] = g.B_[(p0 + q) * g.ldb2 + r % rb + (long long)(r / rb) * g.ldb];
+            }
+        }
+        if (!beta_zero) {
+            for (int e = tid; e < cnt * sc; e += blockDim.x) {
+                const int q = e / sc, r = e - q * sc;
+                sC[e] = g.C_[(p0 + q) * g.ldc2 + r % m + (long long)(r / m) * g.ldc];
+            }
+        }
+        __syncthreads();
+        const int ql = tid / sc, r = tid - ql * sc;
+        const int i = r % m, j = r / m;
+        if (ql < mpr) {
+            for (int q = ql; q < cnt; q += mpr) {
+                A acc = zero_a<A>();
+                if (!alpha_zero) {
+                    const S* a = sA + q * sa;
+                    const S* b = sB + q * sb;
+                    for (int l = 0; l < k; ++l) {
+                        A av = conj_s(to_a(a[ta ? l + k * i : i + m * l]), g.conja);
+                        A bv = conj_s(to_a(b[tb ? j + n * l : l + k * j]), g.conjb);
+                        mac(acc, av, bv);
+                    }
+                }
+                A v = alpha_zero ? zero_a<A>() : mul(alpha, acc);
+                if (!beta_zero) v = axpy(beta, to_a(sC[q * sc + i + m * j]), v);
+                g.C_[(p0 + q) * g.ldc2 + i + (long long)j * g.ldc] = to_s<Ty>(v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class Ty>
+sbgemm_status launch_generic(const Req& r) {
+    Args<Ty> a;
+    fill_args(a, r);
+    using S = typename Ty::S;
+    const int sc = r.m * r.n;
+    const int mpr = 256 / sc;
+    const size_t per = sizeof(S) * (size_t)(r.m * r.k + r.k * r.n + sc);
+    // pairs per tile: up to four compute rounds, within 40 KB of shared memory
+    int P = mpr * 4;
+    if ((size_t)P * per > 40 * 1024) P = (int)((40 * 1024) / per);
+    if (P < 1) P = 1;
+    a.P = P;
+    a.stages = 1;
+    a.flat = 0;
+    const size_t smem = per * P;
+    const long long ntiles = ((long long)r.batch + P - 1) / P;
+    long long grid = (long long)num_sms() * 8;
+    if (grid > ntiles) grid = ntiles;
+    generic_kernel<Ty><<<(unsigned)grid, 256, smem, r.stream>>>(a, r.m, r.n, r.k, r.ta, r.tb);
+    return (sbgemm_status)cudaGetLastError();
+}
+
+// C = beta * C over the m x n blocks (alpha == 0 or k == 0); C is not read
+// when beta == 0.
+template <class Ty>
+__global__ void scale_kernel(Args<Ty> g, int m, int n)
+{
+    using A = typename Ty::A;
+    A beta = g.beta_ptr ? *g.beta_ptr : g.beta;
+    const bool bz = is_zero(beta);
+    const long long total = (long long)g.batch * m * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / (m * n);
+        const int r = (int)(e - p * m * n);
+        const int i = r % m, j = r / m;
+        typename Ty::S* c = g.C_ + p * g.ldc2 + i + (long long)j * g.ldc;
+        *c = to_s<Ty>(bz ? zero_a<A>() : mul(beta, to_a(*c)));
+    }
+}
+
+template <class Ty>
+sbgemm_status launch_scale(const Req& r) {
+    Args<Ty> a;
+    fill_args(a, r);
+    const long long total = (long long)r.batch * r.m * r.n;
+    long long grid = (total + 255) / 256;
+    if (grid > (long long)num_sms() * 16) grid = (long long)num_sms() * 16;
+    if (grid < 1) grid = 1;
+    scale_kernel<Ty><<<(unsigned)grid, 256, 0, r.stream>>>(a, r.m, r.n);
+    return (sbgemm_status)cudaGetLastError();
+}
+
+// ------------------------------------------------------------ shape dispatch
+
+template <class Ty, int M, int N, int K, bool TA, bool TB>
+sbgemm_status launch_shape_op(const Req& r, const LaunchOpts& o) {
+    constexpr TileEntry te = tile_for(Ty::code, M, N, K, TA ? 1 : 0, TB ? 1 : 0);
+    using Cf = Cfg<Ty, M, N, K, TA, TB, te.tm, te.tn, te.si != 0, te.sj != 0, te.nt>;
+    return launch_pipe<Cf>(r, o);
+}
+
+template <class Ty, int M, int N, int K>
+sbgemm_status launch_shape(const Req& r) {
+    if (r.variant >= kNumPipeVariants) return launch_generic<Ty>(r);
+    const LaunchOpts o = pipe_variant(r.variant);
+    if (!r.ta && !r.tb) return launch_shape_op<Ty, M, N, K, false, false>(r, o);
+    if (r.ta && !r.tb)  return launch_shape_op<Ty, M, N, K, true, false>(r, o);
+    if (!r.ta && r.tb)  return launch_shape_op<Ty, M, N, K, false, true>(r, o);
+    return launch_shape_op<Ty, M, N, K, true, true>(r, o);
+}
+
+// Per-type entry used by the C ABI; defined in one translation unit per type.
+sbgemm_status run_S(const Req& r);
+sbgemm_status run_D(const Req& r);
+sbgemm_status run_C(const Req& r);
+sbgemm_status run_Z(const Req& r);
+sbgemm_status run_H(const Req& r);
+sbgemm_status run_B(const Req& r);
+bool has_specialized(int type, int m, int n, int k);
+
+}  // namespace sbg

@@ -1,0 +1,206 @@
+"""Thin ctypes binding over ``libsbgemm.so`` (the C ABI in ``include/sbgemm.h``).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Functions named ``sbgemm_*`` are the C entry points
+themselves (raw integers for pointers); ``gemm_multi_uniform`` is a
+convenience wrapper that takes torch tensors for the device buffers.
+
+Loading fails loudly when the library has not been built; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsbgemm.so")
+
+TYPE_CODES = {"s": 0, "d": 1, "c": 2, "z": 3, "h": 4, "b": 5}
+SCALARS_HOST, SCALARS_DEVICE = 0, 1
+
+STATUS = {0: "SUCCESS", -1: "ERR_INVALID_TRANS", -2: "ERR_INVALID_SIZE", -3: "ERR_INVALID_LD",
+          -4: "ERR_NULL_POINTER", -5: "ERR_INVALID_VALUE", -6: "ERR_TIMEOUT",
+          -7: "ERR_NOT_SUPPORTED", -8: "ERR_CAPACITY"}
+
+# Every symbol include/sbgemm.h declares, with its ctypes signature.
+_c, _i, _ll, _vp = ctypes.c_char, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
+_UNIFORM = [_c, _c, _i, _i, _i, _vp, _vp, _i, _ll, _vp, _i, _ll, _vp, _vp, _i, _ll, _i]
+SIGNATURES = {
+    "sbgemm_Sgemm_multi_uniform": (_i, _UNIFORM),
+    "sbgemm_Dgemm_multi_uniform": (_i, _UNIFORM),
+    "sbgemm_Cgemm_multi_uniform": (_i, _UNIFORM),
+    "sbgemm_Zgemm_multi_uniform": (_i, _UNIFORM),
+    "sbgemm_Sgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_Dgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_Cgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_Zgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_Hgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_Bgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_num_variants": (_i, [_i, _i, _i, _i]),
+    "sbgemm_variant_name": (ctypes.c_char_p, [_i, _i, _i, _i, _i]),
+    "sbgemm_gemm_multi_uniform_variant": (_i, [_i] + _UNIFORM + [_i, _i, _vp]),
+    "sbgemm_set_choice": (_i, [_i] * 9),
+    "sbgemm_get_choice": (_i, [_i] * 8),
+    "sbgemm_clear_choices": (None, []),
+    "sbgemm_status_string": (ctypes.c_char_p, [_i]),
+    "sbgemm_version": (_i, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SbgemmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({status_string(status)})")
+
+
+def lib():
+    """Load the library (once).  Raises if it is missing: no fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().sbgemm_status_string(status).decode()
+    except Exception:
+        return STATUS.get(status, str(status))
+
+
+def __getattr__(name):
+    # the C entry points under their own names
+    if name in SIGNATURES:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+# ---------------------------------------------------------------- helpers
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _scalar_buf(dtype: str, value):
+    """Host scalar for alpha/beta in the storage arithmetic type."""
+    if dtype == "s" or dtype in "hb":
+        return (ctypes.c_float * 1)(float(complex(value).real))
+    if dtype == "d":
+        return (ctypes.c_double * 1)(float(complex(value).real))
+    v = complex(value)
+    if dtype == "c":
+        return (ctypes.c_float * 2)(v.real, v.imag)
+    return (ctypes.c_double * 2)(v.real, v.imag)
+
+
+def gemm_multi_uniform(dtype: str, transa: str, transb: str, m: int, n: int, k: int,
+                       alpha, A, lda: int, lda2: int, B, ldb: int, ldb2: int,
+                       beta, C, ldc: int, ldc2: int, batch: int, stream=None,
+                       variant: int | None = None, device_scalars: bool = False,
+                       check: bool = True) -> int:
+    """Eq. (1) on the Section 4 layout.  A, B, C are torch CUDA tensors (or
+    raw device addresses as int).  alpha/beta are Python numbers (host
+    scalars) or, with ``device_scalars``, device tensors holding one scalar.
+    Returns the status; raises ``SbgemmError`` on a nonzero status when
+    ``check``."""
+    L = lib()
+    t = TYPE_CODES[dtype]
+    if device_scalars:
+        pa, pb, mode = _ptr(alpha), _ptr(beta), SCALARS_DEVICE
+        keep = None
+    else:
+        ab, bb = _scalar_buf(dtype, alpha), _scalar_buf(dtype, beta)
+        keep = (ab, bb)
+        pa, pb, mode = ctypes.addressof(ab), ctypes.addressof(bb), SCALARS_HOST
+    s = _stream_ptr(stream)
+    args = (transa.encode(), transb.encode(), m, n, k, pa, _ptr(A), lda, lda2, _ptr(B), ldb, ldb2,
+            pb, _ptr(C), ldc, ldc2, batch)
+    if variant is None:
+        fn = {"s": L.sbgemm_Sgemm_multi_uniform_async, "d": L.sbgemm_Dgemm_multi_uniform_async,
+              "c": L.sbgemm_Cgemm_multi_uniform_async, "z": L.sbgemm_Zgemm_multi_uniform_async,
+              "h": L.sbgemm_Hgemm_multi_uniform_async, "b": L.sbgemm_Bgemm_multi_uniform_async}[dtype]
+        st = fn(*args, mode, s)
+    else:
+        st = L.sbgemm_gemm_multi_uniform_variant(t, *args, mode, variant, s)
+    del keep
+    if check and st != 0:
+        raise SbgemmError(st, "gemm_multi_uniform")
+    return st
+
+
+def prepare_uniform(dtype: str, transa: str, transb: str, m: int, n: int, k: int,
+                    alpha, A, lda: int, lda2: int, B, ldb: int, ldb2: int,
+                    beta, C, ldc: int, ldc2: int, batch: int, stream=None,
+                    variant: int | None = None):
+    """Bind every argument once and return a no-argument callable that issues
+    the call (host scalars); for timing loops where per-call marshalling
+    would otherwise cost more host time than a small kernel takes."""
+    L = lib()
+    ab, bb = _scalar_buf(dtype, alpha), _scalar_buf(dtype, beta)
+    args = (transa.encode(), transb.encode(), m, n, k, ctypes.addressof(ab), _ptr(A), lda, lda2,
+            _ptr(B), ldb, ldb2, ctypes.addressof(bb), _ptr(C), ldc, ldc2, batch)
+    s = _stream_ptr(stream)
+    if variant is None:
+        fn = {"s": L.sbgemm_Sgemm_multi_uniform_async, "d": L.sbgemm_Dgemm_multi_uniform_async,
+              "c": L.sbgemm_Cgemm_multi_uniform_async, "z": L.sbgemm_Zgemm_multi_uniform_async,
+              "h": L.sbgemm_Hgemm_multi_uniform_async, "b": L.sbgemm_Bgemm_multi_uniform_async}[dtype]
+        full = args + (SCALARS_HOST, s)
+    else:
+        fn = L.sbgemm_gemm_multi_uniform_variant
+        full = (TYPE_CODES[dtype],) + args + (SCALARS_HOST, variant, s)
+
+    def call(_fn=fn, _a=full, _keep=(ab, bb)):
+        st = _fn(*_a)
+        if st != 0:
+            raise SbgemmError(st, "gemm_multi_uniform")
+    return call
+
+
+def num_variants(dtype: str, m: int, n: int, k: int) -> int:
+    return lib().sbgemm_num_variants(TYPE_CODES[dtype], m, n, k)
+
+
+def variant_name(dtype: str, m: int, n: int, k: int, v: int) -> str:
+    return lib().sbgemm_variant_name(TYPE_CODES[dtype], m, n, k, v).decode()
+
+
+def set_choice(dtype, m, n, k, ta, tb, beta_zero, size_class, variant) -> None:
+    st = lib().sbgemm_set_choice(TYPE_CODES[dtype], m, n, k, int(ta), int(tb), int(beta_zero),
+                                 size_class, variant)
+    if st != 0:
+        raise SbgemmError(st, "set_choice")
+
+
+def get_choice(dtype, m, n, k, ta, tb, beta_zero, size_class) -> int:
+    return lib().sbgemm_get_choice(TYPE_CODES[dtype], m, n, k, int(ta), int(tb), int(beta_zero),
+                                   size_class)
+
+
+def clear_choices() -> None:
+    lib().sbgemm_clear_choices()

@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/sbgemm.h declares, and rejects invalid arguments with
+the documented status codes before touching the device."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1304_7053_gb300 import sbgemm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sbgemm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = sbgemm.lib()
+    names = declared_symbols()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(L, name), f"{name} declared but not exported"
+        assert name in sbgemm.SIGNATURES, f"{name} has no binding signature"
+
+
+def test_binding_covers_only_declared_symbols():
+    assert set(sbgemm.SIGNATURES) <= set(declared_symbols())
+
+
+def call(dtype="s", ta="N", tb="N", m=2, n=2, k=2, lda=2, lda2=4, ldb=2, ldb2=4, ldc=2,
+         ldc2=4, batch=1, A=16, B=16, C=16, mode=0, alpha=True, beta=True):
+    a = sbgemm._scalar_buf(dtype, 1.0)
+    b = sbgemm._scalar_buf(dtype, 0.0)
+    L = sbgemm.lib()
+    return L.sbgemm_gemm_multi_uniform_variant(
+        sbgemm.TYPE_CODES[dtype], ta.encode(), tb.encode(), m, n, k,
+        ctypes.addressof(a) if alpha else None, A, lda, lda2, B, ldb, ldb2,
+        ctypes.addressof(b) if beta else None, C, ldc, ldc2, batch, mode, 0, None)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(ta="X"), -1), (dict(tb="q"), -1),
+    (dict(m=17), -2), (dict(k=-1), -2), (dict(batch=-1), -2),
+    (dict(lda=1), -3), (dict(ldc=1), -3), (dict(ldc2=3), -3), (dict(lda2=3), -3),
+    (dict(ta="T", m=3, lda=2, ldc=3, ldc2=6), -3),
+    (dict(C=0), -4), (dict(alpha=False), -4), (dict(A=0), -4),
+    (dict(mode=7), -5), (dict(dtype="z", m=0), 0), (dict(batch=0), 0),
+])
+def test_argument_errors(kw, status):
+    assert call(**kw) == status
+
+
+def test_status_strings_and_version():
+    assert sbgemm.status_string(0) == "success"
+    assert "trans" in sbgemm.status_string(-1)
+    assert sbgemm.lib().sbgemm_version() >= 100
+
+
+def test_variant_table_host_logic():
+    assert sbgemm.num_variants("s", 16, 16, 16) == 7
+    assert sbgemm.num_variants("s", 7, 3, 11) == 1
+    assert sbgemm.num_variants("s", 17, 3, 11) == 0
+    assert "generic" in sbgemm.variant_name("s", 7, 3, 11, 0)
+    sbgemm.clear_choices()
+    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 0
+    sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, 3)
+    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 3
+    sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, -1)
+    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 0
+    with pytest.raises(sbgemm.SbgemmError):
+        sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, 99)
+    sbgemm.clear_choices()
