@@ -179,15 +179,21 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    # Timed region: K steps of 16 eager launches on one stream.  One pair of
+    # CUDA events per step brackets one kernel, rotating over the sizes, so
+    # every kernel is timed K/16 times inside the timed region while the
+    # events add almost nothing to the step.
+    K = args.steps
+    nsz = len(SIZES)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             for m in SIZES:
                 launch(m)
     torch.cuda.synchronize()
-
-    K = args.steps
-    ev = {m: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(K)] for m in SIZES}
+    # short runs (fewer steps than sizes) time every kernel of every step
+    every = K < nsz
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nsz if every else 1)] for _ in range(K)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local_rank)
     barrier()
@@ -197,10 +203,15 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         t0.record(stream)
         for s in range(K):
-            for m in SIZES:
-                ev[m][s][0].record(stream)
-                launch(m)
-                ev[m][s][1].record(stream)
+            jt = s % nsz
+            for j, m in enumerate(SIZES):
+                if every or j == jt:
+                    e = ev[s][j if every else 0]
+                    e[0].record(stream)
+                    launch(m)
+                    e[1].record(stream)
+                else:
+                    launch(m)
         t1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -212,12 +223,42 @@ def run_ours(args, rank, world, local_rank):
         elapsed_ms = float(tt.item())
     ms_step = elapsed_ms / K
     per = {}
-    for m in SIZES:
-        d = [a.elapsed_time(b) for a, b in ev[m]]
+    for j, m in enumerate(SIZES):
+        if every:
+            d = [ev[s][j][0].elapsed_time(ev[s][j][1]) for s in range(K)]
+        else:
+            d = [ev[s][0][0].elapsed_time(ev[s][0][1]) for s in range(K) if s % nsz == j]
+        if not d:
+            continue
         mean_ms = sum(d) / len(d)
-        per[m] = {"us": round(mean_ms * 1e3, 3),
+        per[m] = {"us": round(mean_ms * 1e3, 3), "samples": len(d),
                   "gflops": round(flops_per_pair(m) * N_PAIRS / (mean_ms * 1e-3) / 1e9, 1),
                   "gbps": round(bytes_per_pair(m) * N_PAIRS / (mean_ms * 1e-3) / 1e9, 1)}
+
+    # cross-check: the step replayed from a CUDA graph (no host launch cost)
+    graph_ms = None
+    try:
+        cap = torch.cuda.Stream(device=dev)
+        gcalls = {m: sbgemm.prepare_uniform("s", "N", "N", m, m, m, 1.0, bufs[m][0], m, m * m,
+                                            bufs[m][1], m, m * m, 0.0, bufs[m][2], m, m * m,
+                                            N_PAIRS, stream=cap) for m in SIZES}
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            for m in SIZES:
+                gcalls[m]()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                g.replay()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = min(K, 200)
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = round(e0.elapsed_time(e1) / reps, 5)
+    except Exception as ex:
+        graph_ms = f"unavailable: {type(ex).__name__}"
     total_flops = sum(flops_per_pair(m) * N_PAIRS for m in SIZES)
     total_bytes = sum(bytes_per_pair(m) * N_PAIRS for m in SIZES)
     value = world * total_flops / (ms_step * 1e-3) / 1e9
@@ -233,31 +274,15 @@ def run_ours(args, rank, world, local_rank):
                 "peak_kind": peak_kind,
                 "algorithmic_bytes": bytes_per_pair(dom) * N_PAIRS}
 
-    graph_ms = None
-    try:   # cross-check: the same step replayed from a CUDA graph (no host launch cost)
-        cap = torch.cuda.Stream(device=dev)
-        gcalls = {m: sbgemm.prepare_uniform("s", "N", "N", m, m, m, 1.0, bufs[m][0], m, m * m,
-                                            bufs[m][1], m, m * m, 0.0, bufs[m][2], m, m * m,
-                                            N_PAIRS, stream=cap) for m in SIZES}
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=cap):
-            for m in SIZES:
-                gcalls[m]()
-        for _ in range(3):
-            g.replay()
-        torch.cuda.synchronize()
-        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(10, K // 4)
-        r0.record()
-        for _ in range(reps):
-            g.replay()
-        r1.record()
-        torch.cuda.synchronize()
-        graph_ms = round(r0.elapsed_time(r1) / reps, 5)
-    except Exception as ex:  # graph capture is a cross-check only
-        graph_ms = f"unavailable: {type(ex).__name__}"
-
     e2e = run_e2e(args, bufs, launch, stream, barrier, world, dev) if not args.no_e2e else None
+    vb = None
+    if not args.no_vbatch and rank == 0:
+        try:
+            del bufs
+            torch.cuda.empty_cache()
+            vb = [run_vbatch_bench(d, dev, stream) for d in ("s", "d")]
+        except Exception as ex:
+            vb = f"failed: {type(ex).__name__}: {ex}"
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "GFLOP/s",
         "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -279,37 +304,53 @@ def run_ours(args, rank, world, local_rank):
         "per_size": per,
         "roofline": roofline,
         "gpu_launches": K * len(SIZES),
+        "timing": "eager launches on one stream; per-kernel durations from one event pair "
+                  "per step rotating over the sizes",
         "clocks": clk,
         "e2e": e2e,
+        "vbatch": vb,
     }
     return out
 
 
 def run_e2e(args, bufs, launch, stream, barrier, world, dev):
-    """Same workload with host buffers: every step copies A, B from pinned
-    host memory, runs the C ABI call, and copies C back."""
+    """Same workload with host buffers, through the C ABI's host-array entry
+    point: every step streams A and B from pinned host memory to the device,
+    computes, and copies C back (copies and kernels of consecutive chunks
+    overlap inside the call)."""
+    import ctypes
     import torch
+    from paper_1304_7053_gb300 import sbgemm
     host = {}
     for m in SIZES:
         A, B, C = bufs[m]
-        host[m] = (A.cpu().pin_memory(), B.cpu().pin_memory(), torch.empty_like(C, device="cpu").pin_memory())
+        host[m] = (A.cpu().pin_memory(), B.cpu().pin_memory(),
+                   torch.empty(C.numel(), dtype=C.dtype).pin_memory())
+    work = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    one = (ctypes.c_float * 1)(1.0)
+    zero = (ctypes.c_float * 1)(0.0)
+    L = sbgemm.lib()
+
+    def step():
+        for m in SIZES:
+            hA, hB, hC = host[m]
+            st = L.sbgemm_gemm_multi_uniform_host(0, b"N", b"N", m, m, m, ctypes.addressof(one),
+                                                  hA.data_ptr(), m, m * m, hB.data_ptr(), m, m * m,
+                                                  ctypes.addressof(zero), hC.data_ptr(), m, m * m,
+                                                  N_PAIRS, work.data_ptr(), work.numel(),
+                                                  stream.cuda_stream)
+            if st != 0:
+                raise sbgemm.SbgemmError(st, "gemm_multi_uniform_host")
+
     K = max(3, args.e2e_steps)
-    for it in range(2 + K):
-        if it == 2:
-            barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        with torch.cuda.stream(stream):
-            for m in SIZES:
-                A, B, C = bufs[m]
-                hA, hB, hC = host[m]
-                A.copy_(hA, non_blocking=True)
-                B.copy_(hB, non_blocking=True)
-                launch(m)
-                hC.copy_(C, non_blocking=True)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -319,12 +360,87 @@ def run_e2e(args, bufs, launch, stream, barrier, world, dev):
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
+    # the result read back equals the device path's (same kernels, same inputs)
+    ok = all(torch.equal(host[m][2], bufs[m][2].cpu()) for m in SIZES[-2:])
     total_flops = sum(flops_per_pair(m) * N_PAIRS for m in SIZES)
     h2d = sum(2 * 4 * m * m * N_PAIRS for m in SIZES)
     d2h = sum(4 * m * m * N_PAIRS for m in SIZES)
     return {"value": round(world * total_flops / (ms * 1e-3) / 1e9, 1), "unit": "GFLOP/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K,
-            "ms_per_step": round(ms, 3)}
+            "ms_per_step": round(ms, 3), "link_gbps": round((h2d + d2h) / (ms * 1e-3) / 1e9, 1),
+            "matches_device_result": bool(ok),
+            "path": "sbgemm_gemm_multi_uniform_host, 512 MB device work buffer, pinned host arrays"}
+
+
+# ------------------------------------------------------------------ variable size
+
+def run_vbatch_bench(dtype, dev, stream, reps=20, warm=3, N=1_000_000):
+    """The variable-size batch: N problems, m = n = k = p + 1 with P(p)
+    proportional to 1/p, beta per problem in {0, 1}, back to back in one
+    arena; one plan run (memset + one persistent kernel) against the same
+    problems partitioned by size and run as one fixed-size call per size."""
+    import numpy as np
+    import torch
+    from paper_1304_7053_gb300 import inputs, sbgemm
+    desc, la, lb, lc = inputs.vbatch_problems(N, seed=0)
+    tdt = torch.float32 if dtype == "s" else torch.float64
+    es = 4 if dtype == "s" else 8
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    A = torch.rand(la, device=dev, generator=gen, dtype=tdt) * 2 - 1
+    B = torch.rand(lb, device=dev, generator=gen, dtype=tdt) * 2 - 1
+    C = torch.rand(lc, device=dev, generator=gen, dtype=tdt) * 2 - 1
+    plan = sbgemm.VPlan(dtype, sbgemm.vproblems_from_desc(desc))
+    sizes = desc[:, 0]
+    bz = (desc[:, 3] >> 4) & 1
+    alg_bytes = int(np.sum(es * sizes * sizes * (3 + (1 - bz))))
+    flops = int(np.sum(2 * sizes ** 3))
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            plan.run(1.0, A, B, 1.0, C, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.run(1.0, A, B, 1.0, C, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    v_ms = e0.elapsed_time(e1) / reps
+    info = plan.info()
+    plan.close()
+    # comparator: the paper's partition by size, one uniform call per size
+    # (beta = 1 for every problem: the byte count below includes the C read)
+    calls = []
+    fbytes = 0
+    for sz in range(2, 17):
+        cnt = int(np.sum(sizes == sz))
+        if cnt == 0:
+            continue
+        S = sz * sz
+        a = torch.rand(cnt * S, device=dev, generator=gen, dtype=tdt)
+        b = torch.rand(cnt * S, device=dev, generator=gen, dtype=tdt)
+        c = torch.rand(cnt * S, device=dev, generator=gen, dtype=tdt)
+        calls.append((sbgemm.prepare_uniform(dtype, "N", "N", sz, sz, sz, 1.0, a, sz, S, b, sz, S,
+                                             1.0, c, sz, S, cnt, stream=stream), (a, b, c)))
+        fbytes += es * cnt * S * 4
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            for f, _keep in calls:
+                f()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(reps):
+            for f, _keep in calls:
+                f()
+        f1.record(stream)
+    torch.cuda.synchronize()
+    f_ms = f0.elapsed_time(f1) / reps
+    return {"dtype": dtype, "problems": N, "tiles": info["tiles"], "buckets": info["buckets"],
+            "ms": round(v_ms, 4), "gflops": round(flops / (v_ms * 1e-3) / 1e9, 1),
+            "gbps": round(alg_bytes / (v_ms * 1e-3) / 1e9, 1),
+            "fixed_per_size_ms": round(f_ms, 4),
+            "fixed_per_size_gbps": round(fbytes / (f_ms * 1e-3) / 1e9, 1),
+            "note": "vbatch: mixed beta (C read for half the problems); per-size fixed calls: "
+                    "beta = 1 for all, bytes counted accordingly"}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -403,6 +519,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-vbatch", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time")
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--sizes", default="1-16",

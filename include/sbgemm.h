@@ -68,6 +68,10 @@ enum {
     SBGEMM_SCALARS_DEVICE = 1   /* read by the kernel from device memory */
 };
 
+/* Type codes for the type-erased calls (variants, host arrays, plans). */
+enum { SBGEMM_TYPE_S = 0, SBGEMM_TYPE_D = 1, SBGEMM_TYPE_C = 2, SBGEMM_TYPE_Z = 3,
+       SBGEMM_TYPE_H = 4, SBGEMM_TYPE_B = 5 };
+
 typedef struct { float x, y; } sbgemm_c32;   /* same layout as cuComplex */
 typedef struct { double x, y; } sbgemm_c64;  /* same layout as cuDoubleComplex */
 
@@ -142,15 +146,27 @@ sbgemm_status sbgemm_Bgemm_multi_uniform_async(char transa, char transb, int m, 
     const float* beta, uint16_t* C, int ldc, long long ldc2, int batchCount,
     int scalar_mode, void* stream);
 
+/*
+ * Eq. (1) on HOST arrays (pinned memory gives overlapped copies; pageable
+ * memory works but serialises).  The batch streams through the caller's
+ * device work buffer `dwork` (dwork_bytes, at least two pairs' worth of A,
+ * B and C) in chunks, double-buffered: host->device copies, kernels (on
+ * `stream`) and device->host copies of consecutive chunks overlap on two
+ * internal streams.  The call is ordered after earlier work on `stream` and
+ * later work on `stream` waits for the last copy back; it returns before the
+ * copies finish (synchronise the stream before reading hC).  Host scalars
+ * only; lda2 and ldb2 must be nonzero.  C is copied in when beta != 0 or
+ * when its layout has gaps.  Allocates nothing; SBGEMM_ERR_CAPACITY when
+ * dwork cannot hold two pairs.  Calls that share dwork must be ordered.
+ */
+sbgemm_status sbgemm_gemm_multi_uniform_host(int type, char transa, char transb,
+    int m, int n, int k, const void* alpha, const void* hA, int lda, long long lda2,
+    const void* hB, int ldb, long long ldb2, const void* beta, void* hC, int ldc,
+    long long ldc2, int batchCount, void* dwork, size_t dwork_bytes, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Kernel variants (used by the autotuner and the learned selector).   */
 /* ------------------------------------------------------------------ */
-
-/*
- * Type codes for the variant, tuning and planning calls below.
- */
-enum { SBGEMM_TYPE_S = 0, SBGEMM_TYPE_D = 1, SBGEMM_TYPE_C = 2, SBGEMM_TYPE_Z = 3,
-       SBGEMM_TYPE_H = 4, SBGEMM_TYPE_B = 5 };
 
 /* Number of kernel variants a (type, m, n, k) problem can run with; variant
  * 0 is always the default choice.  Returns 0 for an invalid request. */
@@ -185,7 +201,124 @@ int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb,
 void sbgemm_clear_choices(void);
 
 /* ------------------------------------------------------------------ */
-/* Status and device fault word.                                        */
+/* Variable-size batches (Section 1: matrices of different sizes are     */
+/* partitioned into sets of identical size; here one persistent launch). */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One problem of a variable-size batch: Eq. (1) for C_q = alpha op(A_q)
+ * op(B_q) + beta_q C_q with 0 <= m, n, k <= 16, each matrix stored
+ * column-major with minimal leading dimension (rows of the stored matrix)
+ * at element offset a, b, c of three arenas.  flags: bits 0-1 opA (0 N,
+ * 1 T, 2 C), bits 2-3 opB, bit 4 set = beta_q is 0 for this problem (C_q
+ * is then not read), else beta_q is the call's beta.  32 bytes.
+ */
+typedef struct {
+    int m, n, k;
+    int flags;
+    long long a, b, c;
+} sbgemm_vproblem;
+
+typedef struct sbgemm_vplan_s* sbgemm_vplan;
+
+/*
+ * Build a plan for `count` problems (host array, copied): problems are
+ * bucketed by (m, n, k, opA transposed, opB transposed), each bucket is cut
+ * into tiles, and the tile list and per-problem records are uploaded to
+ * device memory owned by the plan (allocated here, on the current device).
+ * The C_q must not overlap.  Returns SBGEMM_ERR_INVALID_SIZE /
+ * SBGEMM_ERR_INVALID_TRANS for a bad problem (nothing allocated).
+ */
+sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
+                                        const sbgemm_vproblem* problems, int count);
+sbgemm_status sbgemm_vbatch_plan_destroy(sbgemm_vplan plan);
+
+/*
+ * Run a plan: one persistent kernel launch whose blocks take tiles from a
+ * device work queue (an atomic counter reset by a memset node first), so
+ * the whole batch is a memset plus one kernel on `stream` and can be
+ * captured into a CUDA graph.  alpha/beta as for the uniform entry points
+ * (scalar_mode; fp32 scalars for the 16-bit types).  A, B, C are the
+ * arenas.  Concurrent runs of the same plan race on its queue counter.
+ */
+sbgemm_status sbgemm_vbatch_run(sbgemm_vplan plan, const void* alpha, const void* A,
+                                const void* B, const void* beta, void* C,
+                                int scalar_mode, void* stream);
+
+/* Plan statistics: number of tiles, of buckets, and device bytes owned. */
+sbgemm_status sbgemm_vbatch_plan_info(sbgemm_vplan plan, int* n_tiles, int* n_buckets,
+                                      long long* device_bytes);
+
+/* ------------------------------------------------------------------ */
+/* Timing core (autotuner).                                             */
+/* ------------------------------------------------------------------ */
+
+typedef struct sbgemm_timer_s* sbgemm_timer;
+
+/* A set of n_marks CUDA events.  A mark is an external event record, so
+ * marks issued while a stream is being captured become event nodes of the
+ * graph and time every replay. */
+sbgemm_status sbgemm_timer_create(sbgemm_timer* timer, int n_marks);
+sbgemm_status sbgemm_timer_mark(sbgemm_timer timer, int mark, void* stream);
+/* Milliseconds between two marks; waits for mark `to` to complete. */
+sbgemm_status sbgemm_timer_elapsed(sbgemm_timer timer, int from, int to, float* ms);
+sbgemm_status sbgemm_timer_destroy(sbgemm_timer timer);
+
+/*
+ * Median time (ms) of `reps` calls of one kernel variant (host scalars).
+ * When `flush` is not NULL, flush_bytes of it are overwritten before each
+ * call (outside the timed interval) so every call starts with a cold L2.
+ * Synchronises the stream.
+ */
+sbgemm_status sbgemm_time_variant(int type, char transa, char transb, int m, int n, int k,
+    const void* alpha, const void* A, int lda, long long lda2,
+    const void* B, int ldb, long long ldb2, const void* beta, void* C, int ldc,
+    long long ldc2, int batchCount, int variant, int reps, void* flush, size_t flush_bytes,
+    void* stream, float* ms);
+
+/* ------------------------------------------------------------------ */
+/* Learned variant selector: a 3-layer perceptron cost model.           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Network with F inputs, H hidden units (two hidden layers) and V outputs
+ * (one predicted log-time per kernel variant), fp32:
+ *   Z1 = X W1^T + b1, H1 = relu(Z1); Z2 = H1 W2^T + b2, H2 = relu(Z2);
+ *   Y = H2 W3^T + b3.
+ * Parameters are one device buffer, row-major: W1 (H x F), b1 (H),
+ * W2 (H x H), b2 (H), W3 (V x H), b3 (V); sbgemm_mlp_param_count gives its
+ * length in floats (0 for invalid sizes).  X is batch x F, Y batch x V,
+ * row-major, device memory owned by the caller.  The paper has no
+ * counterpart: this selects among this library's kernel variants.
+ */
+long long sbgemm_mlp_param_count(int F, int H, int V);
+
+/* Forward pass.  work: 4*batch*H floats (keeps Z1, H1, Z2, H2 for the
+ * backward pass). */
+sbgemm_status sbgemm_mlp_forward(int F, int H, int V, const float* params, const float* X,
+                                 int batch, float* Y, float* work, void* stream);
+
+/*
+ * Masked mean-squared-error loss and its gradient:
+ *   L = sum mask (Y - T)^2 / (2 M), M = sum mask (L = 0 when M = 0),
+ * back-propagated through the network (relu'(0) = 0).  Y and work come from
+ * sbgemm_mlp_forward with the same X.  grads has the parameter layout;
+ * work2: batch*(V + 2H) floats; loss: 2 floats on the device (L, M).
+ * Reductions run in a fixed order: results are reproducible.
+ */
+sbgemm_status sbgemm_mlp_backward(int F, int H, int V, const float* params, const float* X,
+                                  int batch, const float* Y, const float* T, const float* mask,
+                                  const float* work, float* grads, float* work2, float* loss,
+                                  void* stream);
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) on n parameters; t >= 1 is
+ * the step number used in the bias corrections; m, v are the moment
+ * buffers (zero before the first step). */
+sbgemm_status sbgemm_mlp_adam(long long n, float* params, const float* grads, float* m, float* v,
+                              int t, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Status.                                                              */
 /* ------------------------------------------------------------------ */
 
 /* Static description of a status code (never NULL). */

@@ -8,6 +8,8 @@ thread a TM x TN block of C, the model counts per pair:
     accesses in half-warps, 16-byte accesses in quarter-warps; identical
     addresses broadcast);
   * FMA instructions, including the duplicates of ragged tiles;
+  * how many blocks fit an SM's shared memory (three pipeline stages of one
+    compute round of pairs each) and so how many warps compute at once;
 and picks the configuration with the smallest
   max(issue cycles, shared-memory wavefronts)
 under a register budget for accumulators plus fragments.  Rows and columns of
@@ -22,6 +24,7 @@ from __future__ import annotations
 import itertools
 import os
 import sys
+from math import gcd
 
 TYPES = {  # code: (element bytes, complex, fma per mac, unused)
     0: (4, False, 1, 32),   # S
@@ -32,6 +35,8 @@ TYPES = {  # code: (element bytes, complex, fma per mac, unused)
     5: (2, False, 1, 32),   # B
 }
 REG_LIMIT = 96                   # registers for accumulators plus fragments
+STAGES = 3                       # pipeline depth of the default variant
+SMEM_PER_SM = 227 * 1024
 ISSUE_PER_CLK = 4 * 32 * 0.7     # thread-instructions per clock per SM (4 schedulers, derated)
 
 
@@ -99,14 +104,14 @@ def plan(code, M, N, K, TA, TB, TM, TN, SI, SJ):
 
 def direct_store_width(es, M, N, TM, SI, rag_i):
     """Vector width (elements) for storing a thread's contiguous row block of
-    a C column straight to global memory, or 0 when rows are strided or
-    ragged or the column/matrix strides break 8-byte alignment."""
+    a C column straight to global memory as 16-byte vectors, or 0 when rows
+    are strided or ragged or the strides break 16-byte alignment."""
     if SI or rag_i:
         return 0
     SC = M * N
-    for v in (16 // es, 8 // es):
-        if v >= 1 and TM % v == 0 and M % v == 0 and SC % v == 0:
-            return v
+    v = 16 // es
+    if TM % v == 0 and M % v == 0 and SC % v == 0:
+        return v
     return 0
 
 
@@ -181,12 +186,36 @@ def cost(code, M, N, K, TA, TB, TM, TN, SI, SJ, NT):
     else:
         epi_ins = TPM * TM * TN + 2 * M * N * es / 16
         epi_wf = 2 * M * N / 32 + M * N * es / 128
+    # occupancy: a block holds STAGES tiles of MPR pairs (plus an output tile
+    # when C goes through shared memory); the warps of one tile compute while
+    # the other stages load.  Few computing warps cannot fill the issue slots.
+    quantum = 1
+    for sz in (M * K, K * N, M * N):
+        g = 16
+        b = sz * es
+        while b % g:
+            g //= 2
+        quantum = quantum * (16 // g) // gcd(quantum, 16 // g)
+    P = MPR // quantum * quantum if MPR >= quantum else quantum
+    busy = min(P, MPR) / MPR            # fraction of the round's threads with work
+    bpp_in = (p["SA_P"] + p["SB_P"]) * es
+    out_bpp = 0 if VS else padded(M * N, es) * es
+    cta_smem = STAGES * P * bpp_in + P * out_bpp
+    ctas = min(2048 // NT, SMEM_PER_SM // max(1, cta_smem))
+    if ctas < 1:
+        return None
+    warps = ctas * MPR * TPM * busy / 32.0
+    ipc = min(ISSUE_PER_CLK / 32.0, 0.35 * warps)      # warp-instructions per clock
     # issue: thread-instructions per pair (loads + fma + epilogue, ~20% overhead)
     ins_pair = (TPM * (lds_thread + fma_thread) + epi_ins) * 1.2
-    issue_clk = ins_pair / ISSUE_PER_CLK
+    issue_clk = ins_pair / 32.0 / ipc
     wf_total = wf_per_pair + epi_wf
     score = max(issue_clk, wf_total)
-    return score, dict(p, TPM=TPM, MPR=MPR, wf=wf_total, issue=issue_clk, VS=VS)
+    if ctas == 1:
+        # one block per SM: its barrier-separated phases leave bubbles that no
+        # other block fills
+        score *= 1.3
+    return score, dict(p, TPM=TPM, MPR=MPR, wf=wf_total, issue=issue_clk, VS=VS, ctas=ctas)
 
 
 def choose(code, M, N, K, TA, TB):
@@ -225,7 +254,7 @@ def main(out_path):
                 c = choose(code, M, N, K, TA, TB)
                 lines.append(f"    {{{code}, {M}, {N}, {K}, {TA}, {TB}, {c['TM']}, {c['TN']}, {c['SI']}, "
                              f"{c['SJ']}, {c['NT']}}},  // wf {c['wf']:.1f} issue {c['issue']:.1f} "
-                             f"TPM {c['TPM']} VL {c['VL']} VI {c['VI']} VJ {c['VJ']} VS {c['VS']}")
+                             f"TPM {c['TPM']} VL {c['VL']} VI {c['VI']} VJ {c['VJ']} VS {c['VS']} blocks/SM {c['ctas']}")
     lines += ["};", "",
               "constexpr TileEntry tile_for(int type, int m, int n, int k, int ta, int tb) {",
               "    for (const TileEntry& e : kTileTable)",

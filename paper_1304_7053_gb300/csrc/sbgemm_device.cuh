@@ -198,10 +198,12 @@ struct Cfg {
     // vectors along rows of A (stored m x k) / columns of B (stored n x k)
     static constexpr int VI = (!TA && !SI && !RAG_I) ? pick_vec(ES, TM, M, SA_P) : 1;
     static constexpr int VJ = (TB && !SJ && !RAG_J) ? pick_vec(ES, TN, N, SB_P) : 1;
-    // direct store of contiguous row blocks of C (0: through a shared tile)
+    // direct 16-byte stores of contiguous row blocks of C (0: through a
+    // shared tile and coalesced copy-out; narrower direct stores scatter
+    // partial sectors across matrices and cost more L2 requests than the
+    // shared-memory round trip)
     static constexpr int VS = (SI || RAG_I) ? 0
-        : (16 / ES >= 1 && TM % (16 / ES) == 0 && M % (16 / ES) == 0 && SC % (16 / ES) == 0) ? 16 / ES
-        : (8 / ES >= 1 && TM % (8 / ES) == 0 && M % (8 / ES) == 0 && SC % (8 / ES) == 0) ? 8 / ES : 0;
+        : (TM % (16 / ES) == 0 && M % (16 / ES) == 0 && SC % (16 / ES) == 0) ? 16 / ES : 0;
     static_assert(MPR >= 1, "threads per matrix exceeds block size");
     static_assert(K % VL == 0, "l-chunk must divide k");
 };
@@ -221,17 +223,21 @@ __device__ __forceinline__ void stage_operand(S* sdst, const S* g, long long ld2
         const char* src = reinterpret_cast<const char*>(g + p0 * (long long)SE);
         char* dst = reinterpret_cast<char*>(sdst);
         const int nbytes = cnt * SE * ES;
-        const int nchunks = (nbytes + 15) >> 4;
-        for (int c = tid; c < nchunks; c += NT) {
-            const int b = c << 4;
-            int d = b;
-            if (SP != SE) {              // padded slots: chunks never straddle matrices
-                const int q = b / (SE * ES);
-                d = b + q * (SP - SE) * ES;
+        const int nfull = nbytes >> 4;
+        if (SP == SE) {
+#pragma unroll 4
+            for (int c = tid; c < nfull; c += NT) cp_async16(dst + 16 * c, src + 16 * c, 16);
+        } else {
+            // padded slots: chunks never straddle matrices
+            constexpr int CPM = SE * ES / 16;            // chunks per matrix
+#pragma unroll 4
+            for (int c = tid; c < nfull; c += NT) {
+                const int q = c / CPM;
+                cp_async16(dst + 16 * c + q * (SP - SE) * ES, src + 16 * c, 16);
             }
-            const int rem = nbytes - b;
-            cp_async16(dst + d, src + b, rem < 16 ? rem : 16);
         }
+        if ((nbytes & 15) && tid == 0)                  // ragged last chunk, zero-filled
+            cp_async16(dst + 16 * nfull, src + 16 * nfull, nbytes & 15);
     } else {
         const int n = cnt * SE;
         for (int e = tid; e < n; e += NT) {
@@ -258,14 +264,18 @@ __device__ __forceinline__ void store_operand(S* g, const S* ssrc, long long ld2
         const char* src = reinterpret_cast<const char*>(ssrc);
         const int nbytes = cnt * SE * ES;
         const int nfull = nbytes >> 4;
-        for (int c = tid; c < nfull; c += NT) {
-            const int b = c << 4;
-            int d = b;
-            if (SP != SE) {
-                const int q = b / (SE * ES);
-                d = b + q * (SP - SE) * ES;
+        if (SP == SE) {
+#pragma unroll 4
+            for (int c = tid; c < nfull; c += NT)
+                *reinterpret_cast<uint4*>(dst + 16 * c) = *reinterpret_cast<const uint4*>(src + 16 * c);
+        } else {
+            constexpr int CPM = SE * ES / 16;
+#pragma unroll 4
+            for (int c = tid; c < nfull; c += NT) {
+                const int q = c / CPM;
+                *reinterpret_cast<uint4*>(dst + 16 * c) =
+                    *reinterpret_cast<const uint4*>(src + 16 * c + q * (SP - SE) * ES);
             }
-            *reinterpret_cast<uint4*>(dst + b) = *reinterpret_cast<const uint4*>(src + d);
         }
         // ragged tail (< 16 bytes): element stores; slots are unpadded here
         // because a padded slot size is a multiple of 16 bytes
@@ -422,13 +432,19 @@ __device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__
         }
     }
 
-    // epilogue: alpha*acc, plus beta*C_old unless beta == 0 (C then unread)
-    auto value = [&](int r, int c, A cold) -> S {
-        A v = alpha_one ? acc[r][c] : mul(alpha, acc[r][c]);
-        if (skip_ab) v = zero_a<A>();
-        if (!beta_zero) v = axpy(beta, cold, v);
-        return to_s<typename Cf::Ty>(v);
-    };
+    // epilogue: alpha*acc, plus beta*C_old unless beta == 0 (C then unread).
+    // The three cases are separate loops so no per-element select remains.
+    if (skip_ab) {
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) acc[r][c] = zero_a<A>();
+    } else if (!alpha_one) {
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) acc[r][c] = mul(alpha, acc[r][c]);
+    }
     const S* co = sCold + q * Cf::SC_P;
     if constexpr (Cf::VS > 0) {
         if (direct) {
@@ -441,11 +457,17 @@ __device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__
 #pragma unroll
                 for (int rg = 0; rg < TM; rg += VS) {
                     const int i0 = ti * TM + rg;
-                    A cold[VS];
-                    if (!beta_zero) ldvec<VS>(co + i0 + M * j, cold);
                     S out[VS];
+                    if (beta_zero) {
 #pragma unroll
-                    for (int v = 0; v < VS; ++v) out[v] = value(rg + v, c, beta_zero ? zero_a<A>() : cold[v]);
+                        for (int v = 0; v < VS; ++v) out[v] = to_s<typename Cf::Ty>(acc[rg + v][c]);
+                    } else {
+                        A cold[VS];
+                        ldvec<VS>(co + i0 + M * j, cold);
+#pragma unroll
+                        for (int v = 0; v < VS; ++v)
+                            out[v] = to_s<typename Cf::Ty>(axpy(beta, cold[v], acc[rg + v][c]));
+                    }
                     stvec<VS>(g + i0 + M * j, out);
                 }
             }
@@ -453,14 +475,27 @@ __device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__
         }
     }
     S* o = sOut + q * Cf::SC_P;
+    if (beta_zero) {
 #pragma unroll
-    for (int r = 0; r < TM; ++r) {
-        const int i = Cf::SI ? ti + TI * r : ti * TM + r;
+        for (int r = 0; r < TM; ++r) {
+            const int i = Cf::SI ? ti + TI * r : ti * TM + r;
 #pragma unroll
-        for (int c = 0; c < TN; ++c) {
-            const int j = Cf::SJ ? tj + TJ * c : tj * TN + c;
-            if ((Cf::RAG_I && i >= M) || (Cf::RAG_J && j >= N)) continue;
-            o[i + M * j] = value(r, c, beta_zero ? zero_a<A>() : to_a(co[i + M * j]));
+            for (int c = 0; c < TN; ++c) {
+                const int j = Cf::SJ ? tj + TJ * c : tj * TN + c;
+                if ((Cf::RAG_I && i >= M) || (Cf::RAG_J && j >= N)) continue;
+                o[i + M * j] = to_s<typename Cf::Ty>(acc[r][c]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < TM; ++r) {
+            const int i = Cf::SI ? ti + TI * r : ti * TM + r;
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int j = Cf::SJ ? tj + TJ * c : tj * TN + c;
+                if ((Cf::RAG_I && i >= M) || (Cf::RAG_J && j >= N)) continue;
+                o[i + M * j] = to_s<typename Cf::Ty>(axpy(beta, to_a(co[i + M * j]), acc[r][c]));
+            }
         }
     }
 }

@@ -179,11 +179,18 @@ inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool 
     const size_t per_pair = in_bpp * o.stages + out_bpp;
     const size_t cap = 200 * 1024;
     auto round_up = [&](int p) { return (p + quantum - 1) / quantum * quantum; };
+    // R whole compute rounds, rounded down to the quantum (a few idle threads
+    // in the last round) rather than up (a nearly empty extra round)
+    auto rounds_to_P = [&](int R) {
+        const int want = Cf::MPR * R;
+        const int down = want / quantum * quantum;
+        return down >= quantum ? down : round_up(want);
+    };
     int R = (int)(o.tile_bytes / ((size_t)Cf::MPR * in_bpp));
     if (R < 1) R = 1;
-    int P = round_up(Cf::MPR * R);
+    int P = rounds_to_P(R);
     while (P > quantum && (size_t)P * per_pair > cap) {
-        if (R > 1) { --R; P = round_up(Cf::MPR * R); }
+        if (R > 1) { --R; P = rounds_to_P(R); }
         else P = (P - 1) / quantum * quantum;
     }
     if (P < quantum) P = quantum;

@@ -38,12 +38,30 @@ SIGNATURES = {
     "sbgemm_Zgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
     "sbgemm_Hgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
     "sbgemm_Bgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
+    "sbgemm_gemm_multi_uniform_host": (_i, [_i] + _UNIFORM + [_vp, ctypes.c_size_t, _vp]),
     "sbgemm_num_variants": (_i, [_i, _i, _i, _i]),
     "sbgemm_variant_name": (ctypes.c_char_p, [_i, _i, _i, _i, _i]),
     "sbgemm_gemm_multi_uniform_variant": (_i, [_i] + _UNIFORM + [_i, _i, _vp]),
     "sbgemm_set_choice": (_i, [_i] * 9),
     "sbgemm_get_choice": (_i, [_i] * 8),
     "sbgemm_clear_choices": (None, []),
+    "sbgemm_vbatch_plan_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _i]),
+    "sbgemm_vbatch_plan_destroy": (_i, [_vp]),
+    "sbgemm_vbatch_run": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
+    "sbgemm_vbatch_plan_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                     ctypes.POINTER(_ll)]),
+    "sbgemm_timer_create": (_i, [ctypes.POINTER(_vp), _i]),
+    "sbgemm_timer_mark": (_i, [_vp, _i, _vp]),
+    "sbgemm_timer_elapsed": (_i, [_vp, _i, _i, ctypes.POINTER(ctypes.c_float)]),
+    "sbgemm_timer_destroy": (_i, [_vp]),
+    "sbgemm_time_variant": (_i, [_i] + _UNIFORM + [_i, _i, _vp, ctypes.c_size_t, _vp,
+                                                   ctypes.POINTER(ctypes.c_float)]),
+    "sbgemm_mlp_param_count": (_ll, [_i, _i, _i]),
+    "sbgemm_mlp_forward": (_i, [_i, _i, _i, _vp, _vp, _i, _vp, _vp, _vp]),
+    "sbgemm_mlp_backward": (_i, [_i, _i, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                 _vp]),
+    "sbgemm_mlp_adam": (_i, [_ll, _vp, _vp, _vp, _vp, _i, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, _vp]),
     "sbgemm_status_string": (ctypes.c_char_p, [_i]),
     "sbgemm_version": (_i, []),
 }
@@ -204,3 +222,107 @@ def get_choice(dtype, m, n, k, ta, tb, beta_zero, size_class) -> int:
 
 def clear_choices() -> None:
     lib().sbgemm_clear_choices()
+
+
+# ---------------------------------------------------------------- variable size
+
+def vproblem_dtype():
+    """numpy layout of ``sbgemm_vproblem`` (32 bytes)."""
+    import numpy as np
+    return np.dtype([("m", "<i4"), ("n", "<i4"), ("k", "<i4"), ("flags", "<i4"),
+                     ("a", "<i8"), ("b", "<i8"), ("c", "<i8")])
+
+
+def vproblems_from_desc(desc):
+    """Convert an (count, 8) int64 table (m, n, k, flags, offA, offB, offC, 0)
+    into an array of ``sbgemm_vproblem`` records."""
+    import numpy as np
+    desc = np.asarray(desc, dtype=np.int64)
+    out = np.zeros(desc.shape[0], dtype=vproblem_dtype())
+    for i, f in enumerate(("m", "n", "k", "flags")):
+        out[f] = desc[:, i].astype(np.int32)
+    out["a"], out["b"], out["c"] = desc[:, 4], desc[:, 5], desc[:, 6]
+    return out
+
+
+class VPlan:
+    """A variable-size batch plan (``sbgemm_vbatch_plan_create``)."""
+
+    def __init__(self, dtype: str, problems):
+        import numpy as np
+        self.dtype = dtype
+        problems = np.ascontiguousarray(problems, dtype=vproblem_dtype())
+        self._h = ctypes.c_void_p()
+        st = lib().sbgemm_vbatch_plan_create(ctypes.byref(self._h), TYPE_CODES[dtype],
+                                             problems.ctypes.data if problems.size else None,
+                                             int(problems.size))
+        if st != 0:
+            self._h = None
+            raise SbgemmError(st, "vbatch_plan_create")
+
+    def info(self):
+        nt, nb, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        st = lib().sbgemm_vbatch_plan_info(self._h, ctypes.byref(nt), ctypes.byref(nb),
+                                           ctypes.byref(by))
+        if st != 0:
+            raise SbgemmError(st, "vbatch_plan_info")
+        return {"tiles": nt.value, "buckets": nb.value, "device_bytes": by.value}
+
+    def run(self, alpha, A, B, beta, C, stream=None, device_scalars=False, check=True):
+        if device_scalars:
+            pa, pb, mode, keep = _ptr(alpha), _ptr(beta), SCALARS_DEVICE, None
+        else:
+            ab, bb = _scalar_buf(self.dtype, alpha), _scalar_buf(self.dtype, beta)
+            pa, pb, mode, keep = ctypes.addressof(ab), ctypes.addressof(bb), SCALARS_HOST, (ab, bb)
+        st = lib().sbgemm_vbatch_run(self._h, pa, _ptr(A), _ptr(B), pb, _ptr(C), mode,
+                                     _stream_ptr(stream))
+        del keep
+        if check and st != 0:
+            raise SbgemmError(st, "vbatch_run")
+        return st
+
+    def close(self):
+        if self._h:
+            lib().sbgemm_vbatch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Timer:
+    """CUDA-event marks (``sbgemm_timer_*``); marks issued on a capturing
+    stream become event nodes of the graph and time every replay."""
+
+    def __init__(self, n_marks: int):
+        self._h = ctypes.c_void_p()
+        st = lib().sbgemm_timer_create(ctypes.byref(self._h), int(n_marks))
+        if st != 0:
+            self._h = None
+            raise SbgemmError(st, "timer_create")
+
+    def mark(self, i: int, stream=None) -> None:
+        st = lib().sbgemm_timer_mark(self._h, int(i), _stream_ptr(stream))
+        if st != 0:
+            raise SbgemmError(st, "timer_mark")
+
+    def elapsed(self, i: int, j: int) -> float:
+        ms = ctypes.c_float()
+        st = lib().sbgemm_timer_elapsed(self._h, int(i), int(j), ctypes.byref(ms))
+        if st != 0:
+            raise SbgemmError(st, "timer_elapsed")
+        return float(ms.value)
+
+    def close(self):
+        if self._h:
+            lib().sbgemm_timer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

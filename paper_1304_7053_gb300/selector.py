@@ -1,0 +1,287 @@
+"""Autotuner and learned variant selector.
+
+The autotuner times every kernel variant of a problem class with the
+library's native timing core (``sbgemm_time_variant``: CUDA events, L2
+flushed before every call) and appends the medians to a JSONL timing
+database keyed by device, shape and variant; a resumed run skips rows it
+already has.  The exhaustive choice per class is the fastest measured
+variant.
+
+The learned selector is a 3-layer perceptron (``sbgemm_mlp_*`` kernels,
+fp32) that maps problem features to one predicted log-time per variant.  It
+is trained on the database with the library's own forward, backward and Adam
+kernels; at selection time the variant with the smallest prediction among
+the valid ones wins and is installed in the library's selection table.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+
+import numpy as np
+
+from . import inputs, sbgemm
+
+DTYPES = ["s", "d", "c", "z", "h", "b"]
+NFEAT = 16
+NVAR = 9          # variants of specialised shapes; generic shapes have fewer
+HIDDEN = 64
+TORCH_DT = {"s": "float32", "d": "float64", "c": "float32", "z": "float64",
+            "h": "float16", "b": "bfloat16"}
+
+
+def features(dtype, m, n, k, ta, tb, conj, beta0, N) -> np.ndarray:
+    f = np.zeros(NFEAT, dtype=np.float32)
+    f[0], f[1], f[2] = m / 16.0, n / 16.0, k / 16.0
+    f[3] = (math.log10(max(1, N)) - 4.5) / 1.5
+    f[4 + DTYPES.index(dtype)] = 1.0
+    f[10], f[11], f[12], f[13] = float(ta), float(tb), float(conj), float(beta0)
+    f[14] = 1.0 if sbgemm.num_variants(dtype, m, n, k) > 3 else 0.0
+    f[15] = (m * n * k) ** (1.0 / 3.0) / 16.0
+    return f
+
+
+def size_class(N: int) -> int:
+    c = 0
+    while N >= 10 and c < 7:
+        N //= 10
+        c += 1
+    return c
+
+
+# ---------------------------------------------------------------- timing DB
+
+class TimingDB:
+    """Append-only JSONL file of measured variant times."""
+
+    def __init__(self, path: str | None):
+        self.path = path
+        self.rows: list[dict] = []
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.rows = [json.loads(l) for l in f if l.strip()]
+        self._keys = {self.key(r) for r in self.rows}
+
+    @staticmethod
+    def key(r):
+        return (r["device"], r["dtype"], r["m"], r["n"], r["k"], r["ta"], r["tb"], r["conj"],
+                r["beta0"], r["N"], r["variant"])
+
+    def has(self, r) -> bool:
+        return self.key(r) in self._keys
+
+    def add(self, r: dict) -> None:
+        self.rows.append(r)
+        self._keys.add(self.key(r))
+        if self.path:
+            with open(self.path, "a") as f:
+                f.write(json.dumps(r) + "\n")
+
+
+def device_name() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}/{p.multi_processor_count}sm"
+
+
+class Tuner:
+    """Times every variant of a problem class on the current GPU."""
+
+    def __init__(self, db: TimingDB, reps: int = 5, flush_bytes: int = 256 << 20):
+        import torch
+        self.torch = torch
+        self.db = db
+        self.reps = reps
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.flush = torch.empty(flush_bytes, dtype=torch.uint8, device=self.dev)
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.name = device_name()
+
+    def _buffers(self, dtype, m, n, k, ta, tb, N):
+        torch = self.torch
+        ar, ac = inputs.stored_shape("T" if ta else "N", m, k)
+        br, bc = inputs.stored_shape("T" if tb else "N", k, n)
+        dt = getattr(torch, TORCH_DT[dtype])
+        mult = 2 if dtype in "cz" else 1
+        mk = lambda cnt: (torch.rand(max(1, cnt * mult), device=self.dev, dtype=torch.float32) * 2 - 1).to(dt)
+        return (mk(ar * ac * N), mk(br * bc * N), mk(m * n * N)), (max(1, ar), ar * ac,
+                                                                 max(1, br), br * bc, max(1, m), m * n)
+
+    def time_class(self, dtype, m, n, k, ta, tb, conj, beta0, N) -> list[float]:
+        """Median ms of every variant; cached in (and read from) the DB."""
+        nv = sbgemm.num_variants(dtype, m, n, k)
+        out = [None] * nv
+        base = dict(device=self.name, dtype=dtype, m=m, n=n, k=k, ta=int(ta), tb=int(tb),
+                    conj=int(conj), beta0=int(beta0), N=int(N))
+        todo = []
+        for v in range(nv):
+            r = dict(base, variant=v)
+            hit = [x for x in self.db.rows if TimingDB.key(x) == TimingDB.key(dict(r, ms=0))] \
+                if self.db.has(r) else []
+            if hit:
+                out[v] = hit[-1]["ms"]
+            else:
+                todo.append(v)
+        if not todo:
+            return out
+        (A, B, C), (lda, lda2, ldb, ldb2, ldc, ldc2) = self._buffers(dtype, m, n, k, ta, tb, N)
+        opa = ("C" if conj else "T") if ta else "N"
+        opb = ("C" if conj else "T") if tb else "N"
+        ab = sbgemm._scalar_buf(dtype, 1.5)
+        bb = sbgemm._scalar_buf(dtype, 0.0 if beta0 else -0.5)
+        L = sbgemm.lib()
+        ms = ctypes.c_float()
+        for v in todo:
+            st = L.sbgemm_time_variant(sbgemm.TYPE_CODES[dtype], opa.encode(), opb.encode(), m, n, k,
+                                       ctypes.addressof(ab), A.data_ptr(), lda, lda2, B.data_ptr(),
+                                       ldb, ldb2, ctypes.addressof(bb), C.data_ptr(), ldc, ldc2,
+                                       N, v, self.reps, self.flush.data_ptr(), self.flush.numel(),
+                                       self.stream.cuda_stream, ctypes.byref(ms))
+            if st != 0:
+                raise sbgemm.SbgemmError(st, "time_variant")
+            out[v] = float(ms.value)
+            self.db.add(dict(base, variant=v, ms=out[v]))
+        return out
+
+
+def random_classes(count: int, seed: int, dtypes=("s", "d", "c", "z", "h", "b"),
+                   square_frac: float = 0.5):
+    """Random problem classes: m, n, k in 1..16 (half of them square or one of
+    the specialised rectangular shapes), N log-uniform in 1e3..1e6, random
+    dtype, ops and beta == 0."""
+    rect = [(3, 9, 3), (4, 16, 4), (16, 16, 1), (9, 16, 9), (16, 8, 16)]
+    r = inputs.splitmix64(seed, 10 * count).reshape(count, 10)
+    u = (r >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    out = []
+    for i in range(count):
+        if u[i, 0] < square_frac:
+            if u[i, 1] < 0.8:
+                s = 1 + int(u[i, 2] * 16)
+                m = n = k = s
+            else:
+                m, n, k = rect[int(u[i, 2] * len(rect))]
+        else:
+            m, n, k = (1 + int(u[i, j] * 16) for j in (3, 4, 5))
+        N = int(round(10 ** (3 + 3 * u[i, 6])))
+        dtype = dtypes[int(u[i, 7] * len(dtypes))]
+        ta, tb = int(u[i, 8] * 2), int(u[i, 9] * 2)
+        conj = int(dtype in "cz" and (int(r[i, 0]) & 1) == 1)
+        beta0 = int((int(r[i, 1]) >> 3) & 1)
+        out.append((dtype, m, n, k, ta, tb, conj, beta0, N))
+    return out
+
+
+# ---------------------------------------------------------------- the network
+
+class CostModel:
+    """The MLP, trained and evaluated with the library's CUDA kernels."""
+
+    def __init__(self, F=NFEAT, H=HIDDEN, V=NVAR, seed=0):
+        import torch
+        self.torch = torch
+        self.F, self.H, self.V = F, H, V
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.n = int(sbgemm.lib().sbgemm_mlp_param_count(F, H, V))
+        p = np.zeros(self.n, dtype=np.float32)
+        d = inputs.uniform(seed, H * F + H * H + V * H)
+        # weights uniform with variance 1/fan_in, biases 0
+        p[:H * F] = d[:H * F] * math.sqrt(3.0 / F)
+        o = H * F + H
+        p[o:o + H * H] = d[H * F:H * F + H * H] * math.sqrt(3.0 / H)
+        o += H * H + H
+        p[o:o + V * H] = d[H * F + H * H:] * math.sqrt(3.0 / H)
+        self.params = torch.from_numpy(p).to(self.dev)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self.mu = None
+        self.sd = None
+
+    def _check(self, st, where):
+        if st != 0:
+            raise sbgemm.SbgemmError(st, where)
+
+    def forward(self, X):
+        torch = self.torch
+        X = X.contiguous()
+        B = X.shape[0]
+        Y = torch.empty(B, self.V, device=self.dev)
+        work = torch.empty(4 * B * self.H, device=self.dev)
+        s = torch.cuda.current_stream().cuda_stream
+        self._check(sbgemm.lib().sbgemm_mlp_forward(self.F, self.H, self.V, self.params.data_ptr(),
+                                                    X.data_ptr(), B, Y.data_ptr(), work.data_ptr(), s),
+                    "mlp_forward")
+        return Y, work
+
+    def step(self, X, T, mask, lr=3e-3):
+        """One full-batch training step; returns the loss (device tensor)."""
+        torch = self.torch
+        B = X.shape[0]
+        Y, work = self.forward(X)
+        work2 = torch.empty(B * (self.V + 2 * self.H), device=self.dev)
+        loss = torch.empty(2, device=self.dev)
+        s = torch.cuda.current_stream().cuda_stream
+        L = sbgemm.lib()
+        self._check(L.sbgemm_mlp_backward(self.F, self.H, self.V, self.params.data_ptr(),
+                                          X.data_ptr(), B, Y.data_ptr(), T.data_ptr(),
+                                          mask.data_ptr(), work.data_ptr(), self.grads.data_ptr(),
+                                          work2.data_ptr(), loss.data_ptr(), s), "mlp_backward")
+        self.t += 1
+        self._check(L.sbgemm_mlp_adam(self.n, self.params.data_ptr(), self.grads.data_ptr(),
+                                      self.m.data_ptr(), self.v.data_ptr(), self.t, lr, 0.9, 0.999,
+                                      1e-8, s), "mlp_adam")
+        return loss
+
+    # -------- training on timing data
+    def fit(self, feats: np.ndarray, times: np.ndarray, steps=2000, lr=3e-3):
+        """feats: (B, F); times: (B, V) ms with NaN where a variant was not
+        timed.  Targets are standardised log-times."""
+        torch = self.torch
+        lt = np.log(np.where(np.isfinite(times), times, 1.0))
+        mask = np.isfinite(times).astype(np.float32)
+        self.mu = float((lt * mask).sum() / mask.sum())
+        self.sd = float(np.sqrt(((lt - self.mu) ** 2 * mask).sum() / mask.sum())) or 1.0
+        T = torch.from_numpy(((lt - self.mu) / self.sd * mask).astype(np.float32)).to(self.dev)
+        X = torch.from_numpy(feats.astype(np.float32)).to(self.dev)
+        Mk = torch.from_numpy(mask).to(self.dev)
+        hist = []
+        for i in range(steps):
+            loss = self.step(X, T, Mk, lr)
+            if i % 100 == 0 or i == steps - 1:
+                hist.append(float(loss[0].item()))
+        return hist
+
+    def predict_ms(self, feats: np.ndarray) -> np.ndarray:
+        X = self.torch.from_numpy(feats.astype(np.float32)).to(self.dev)
+        Y, _ = self.forward(X)
+        return np.exp(Y.cpu().numpy().astype(np.float64) * self.sd + self.mu)
+
+    def choose(self, feats: np.ndarray, nvalid: np.ndarray) -> np.ndarray:
+        pred = self.predict_ms(feats)
+        idx = np.arange(pred.shape[1])[None, :]
+        pred = np.where(idx < nvalid[:, None], pred, np.inf)
+        return np.argmin(pred, axis=1)
+
+
+def table_from_db(rows):
+    """Group DB rows into (class, times[NVAR]) with NaN for missing variants."""
+    by = {}
+    for r in rows:
+        key = (r["dtype"], r["m"], r["n"], r["k"], r["ta"], r["tb"], r["conj"], r["beta0"], r["N"])
+        by.setdefault(key, np.full(NVAR, np.nan))[r["variant"]] = r["ms"]
+    return by
+
+
+def regret(times: np.ndarray, chosen: np.ndarray) -> np.ndarray:
+    """t(chosen) / t(best) - 1 per class."""
+    best = np.nanmin(times, axis=1)
+    return times[np.arange(times.shape[0]), chosen] / best - 1.0
+
+
+def install(classes, choices) -> None:
+    """Write choices into the library's selection table."""
+    for (dtype, m, n, k, ta, tb, conj, beta0, N), v in zip(classes, choices):
+        sbgemm.set_choice(dtype, m, n, k, ta, tb, beta0, size_class(N), int(v))

@@ -11,8 +11,9 @@ complex, whose real and imaginary parts are dot products of length 2k),
 alpha and the beta update add at most 3 more; max(2k, k+3) equals the
 literal 2ku for k >= 3 and covers k = 1, 2 where 2ku is below the k + 2
 roundings the evaluation can take.  16-bit storage adds the final rounding
-of the fp32 result to the 16-bit format: u16 |C_ref| + (1 + u16) * bound32,
-u16 = 2^-11 (binary16) or 2^-8 (bfloat16).
+of the fp32 result to the 16-bit format: u16 |C_ref| + (1 + u16) * bound32
++ s16, u16 = 2^-11 (binary16) or 2^-8 (bfloat16), s16 half the subnormal
+spacing (2^-25, 2^-134) for results below the normal range.
 """
 from __future__ import annotations
 
@@ -26,6 +27,9 @@ from tests import refmath
 U = {"s": 2.0 ** -24, "c": 2.0 ** -24, "d": 2.0 ** -53, "z": 2.0 ** -53,
      "h": 2.0 ** -24, "b": 2.0 ** -24}
 U16 = {"h": 2.0 ** -11, "b": 2.0 ** -8}
+# half the spacing of the 16-bit subnormals: the absolute rounding error of a
+# result below the normal range
+SUB16 = {"h": 2.0 ** -25, "b": 2.0 ** -134}
 
 
 def dev():
@@ -121,7 +125,7 @@ def bound(b: inputs.UniformBatch, alpha, beta, ref_blocks: np.ndarray, **kw) -> 
     c = (2 * k + 5) if b.dtype in "cz" else max(2 * k, k + 3)
     bd = c * u * s
     if b.dtype in "hb":
-        bd = U16[b.dtype] * np.abs(ref_blocks) + (1 + U16[b.dtype]) * bd
+        bd = U16[b.dtype] * np.abs(ref_blocks) + (1 + U16[b.dtype]) * bd + SUB16[b.dtype]
     return bd
 
 

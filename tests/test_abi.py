@@ -80,3 +80,18 @@ def test_variant_table_host_logic():
     with pytest.raises(sbgemm.SbgemmError):
         sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, 99)
     sbgemm.clear_choices()
+
+
+def test_vbatch_plan_rejects_bad_problems():
+    import numpy as np
+    p = np.zeros(2, dtype=sbgemm.vproblem_dtype())
+    p["m"], p["n"], p["k"] = 3, 3, 3
+    p[1]["m"] = 17
+    with pytest.raises(sbgemm.SbgemmError) as e:
+        sbgemm.VPlan("s", p)
+    assert e.value.status == -2
+    p[1]["m"] = 3
+    p[1]["flags"] = 3          # op code 3 is not N, T or C
+    with pytest.raises(sbgemm.SbgemmError) as e:
+        sbgemm.VPlan("s", p)
+    assert e.value.status == -1

@@ -1,0 +1,118 @@
+"""The learned selector: its CUDA forward / backward / Adam kernels against the
+fp64 reference in oracle/mlp.py, and the selection regret of the trained
+network against the default variant, with the exhaustive autotuner as the
+judge."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp
+from paper_1304_7053_gb300 import inputs, sbgemm, selector
+
+pytestmark = pytest.mark.gpu
+
+
+def unpack(p, F, H, V):
+    o = 0
+    out = {}
+    for name, shape in (("W1", (H, F)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)),
+                        ("W3", (V, H)), ("b3", (V,))):
+        size = int(np.prod(shape))
+        out[name] = p[o:o + size].reshape(shape).astype(np.float64)
+        o += size
+    return out
+
+
+def random_problem(F=16, H=64, V=9, B=300, seed=0):
+    net = selector.CostModel(F, H, V, seed=seed)
+    # nonzero biases so every path is exercised
+    pb = net.params.cpu().numpy()
+    d = inputs.uniform(seed + 5, pb.size) * 0.1
+    pb = pb + d.astype(np.float32)
+    net.params.copy_(torch.from_numpy(pb))
+    X = inputs.uniform(seed + 1, B * F).reshape(B, F).astype(np.float32)
+    T = inputs.uniform(seed + 2, B * V).reshape(B, V).astype(np.float32)
+    mask = (inputs.splitmix64(seed + 3, B * V) % np.uint64(3) != 0).astype(np.float32).reshape(B, V)
+    return net, X, T, mask
+
+
+def test_forward_backward_match_fp64_reference():
+    F, H, V = 16, 64, 9
+    net, X, T, mask = random_problem(F, H, V)
+    dev = net.dev
+    Xd, Td, Md = (torch.from_numpy(a).to(dev) for a in (X, T, mask))
+    Y, work = net.forward(Xd)
+    B = X.shape[0]
+    work2 = torch.empty(B * (V + 2 * H), device=dev)
+    loss = torch.empty(2, device=dev)
+    st = sbgemm.lib().sbgemm_mlp_backward(F, H, V, net.params.data_ptr(), Xd.data_ptr(), B,
+                                          Y.data_ptr(), Td.data_ptr(), Md.data_ptr(),
+                                          work.data_ptr(), net.grads.data_ptr(),
+                                          work2.data_ptr(), loss.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    p = unpack(net.params.cpu().numpy(), F, H, V)
+    Yr, cache = mlp.forward(p, X.astype(np.float64))
+    np.testing.assert_allclose(Y.cpu().numpy(), Yr, rtol=1e-4, atol=1e-5)
+    Lr = mlp.loss(Yr, T.astype(np.float64), mask.astype(np.float64))
+    assert abs(float(loss[0]) - Lr) <= 1e-5 * max(1.0, abs(Lr))
+    assert float(loss[1]) == float(mask.sum())
+    gr = mlp.backward(p, cache, Yr, T.astype(np.float64), mask.astype(np.float64))
+    g = unpack(net.grads.cpu().numpy(), F, H, V)
+    for name in mlp.PARAM_NAMES:
+        scale = np.abs(gr[name]).max() + 1e-12
+        err = np.abs(g[name] - gr[name]).max() / scale
+        assert err < 2e-4, (name, err)
+
+
+def test_adam_matches_reference():
+    F, H, V = 16, 64, 9
+    net, X, T, mask = random_problem(F, H, V, seed=3)
+    p0 = unpack(net.params.cpu().numpy(), F, H, V)
+    Xd, Td, Md = (torch.from_numpy(a).to(net.dev) for a in (X, T, mask))
+    state = {}
+    pr = {k: v.copy() for k, v in p0.items()}
+    for _ in range(3):
+        net.step(Xd, Td, Md, lr=1e-2)
+        Yr, cache = mlp.forward(pr, X.astype(np.float64))
+        mlp.adam_step(pr, mlp.backward(pr, cache, Yr, T.astype(np.float64),
+                                       mask.astype(np.float64)), state, 1e-2)
+    torch.cuda.synchronize()
+    g = unpack(net.params.cpu().numpy(), F, H, V)
+    for name in mlp.PARAM_NAMES:
+        # three steps of size ~lr each; fp32 vs fp64 differences stay far below lr
+        assert np.abs(g[name] - pr[name]).max() < 1e-3, name
+
+
+def test_learned_selector_regret():
+    """Train on autotuner timings of random problem classes, evaluate on
+    held-out classes: the network's mean regret (vs the exhaustive best) must
+    not exceed the default variant's."""
+    db = selector.TimingDB(None)
+    tuner = selector.Tuner(db, reps=3, flush_bytes=192 << 20)
+    train = selector.random_classes(160, seed=11, dtypes=("s", "c"))
+    test = selector.random_classes(60, seed=12, dtypes=("s", "c"))
+
+    def table(classes):
+        F = np.stack([selector.features(*c) for c in classes])
+        Tm = np.full((len(classes), selector.NVAR), np.nan)
+        nv = np.zeros(len(classes), dtype=np.int64)
+        for i, c in enumerate(classes):
+            t = tuner.time_class(*c)
+            Tm[i, :len(t)] = t
+            nv[i] = len(t)
+        return F, Tm, nv
+
+    Ftr, Ttr, _ = table(train)
+    Fte, Tte, nvte = table(test)
+    net = selector.CostModel(seed=1)
+    hist = net.fit(Ftr, Ttr, steps=1500)
+    assert hist[-1] < hist[0]
+    chosen = net.choose(Fte, nvte)
+    r_mlp = selector.regret(Tte, chosen)
+    r_def = selector.regret(Tte, np.zeros(len(test), dtype=np.int64))
+    assert np.all(np.isfinite(r_mlp))
+    assert r_mlp.mean() <= r_def.mean() + 0.02, (r_mlp.mean(), r_def.mean())

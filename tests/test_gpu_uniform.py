@@ -271,3 +271,58 @@ def test_million_pairs_size16_sampled():
     sub.C = b.C.reshape(N, S)[pick].ravel().copy()
     H.assert_parity(sub, got.reshape(N, S)[pick].ravel().copy(), H.oracle_ref(sub, 1.5, -0.5),
                     1.5, -0.5)
+
+
+@pytest.mark.parametrize("dtype,pad", [("s", 0), ("d", 0), ("c", 1), ("z", 2), ("b", 0)])
+def test_host_array_entry_point(dtype, pad):
+    """Host arrays streamed through a small device work buffer (many chunks,
+    double-buffered): same result as the oracle, gaps of a padded C intact."""
+    import ctypes
+    m, N = 9, 3001
+    alpha, beta = (1.5 - 0.5j, -0.5 + 0.25j) if dtype in "cz" else (1.5, -0.5)
+    b = inputs.UniformBatch(dtype, "T", "N", m, m, m, N, seed=71, pad_ld=pad, pad_ld2=pad)
+    hA = torch.from_numpy(b.A.view(np.uint8).copy()).pin_memory()
+    hB = torch.from_numpy(b.B.view(np.uint8).copy()).pin_memory()
+    hC = torch.from_numpy(b.C.view(np.uint8).copy()).pin_memory()
+    work = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    ab, bb = sbgemm._scalar_buf(dtype, alpha), sbgemm._scalar_buf(dtype, beta)
+    s = torch.cuda.current_stream()
+    st = sbgemm.lib().sbgemm_gemm_multi_uniform_host(
+        sbgemm.TYPE_CODES[dtype], b"T", b"N", m, m, m, ctypes.addressof(ab), hA.data_ptr(), b.lda,
+        b.lda2, hB.data_ptr(), b.ldb, b.ldb2, ctypes.addressof(bb), hC.data_ptr(), b.ldc, b.ldc2, N,
+        work.data_ptr(), work.numel(), s.cuda_stream)
+    assert st == 0
+    s.synchronize()
+    got = hC.numpy().view(b.C.dtype).copy()
+    H.assert_parity(b, got, H.oracle_ref(b, alpha, beta), alpha, beta)
+    # beta = 0 with a flat C: C is not copied in (NaN there must not matter)
+    b0 = inputs.UniformBatch(dtype, "N", "N", m, m, m, N, seed=72)
+    hC0 = torch.full((b0.C.nbytes,), 0xFF, dtype=torch.uint8).pin_memory()
+    hA0 = torch.from_numpy(b0.A.view(np.uint8).copy()).pin_memory()
+    hB0 = torch.from_numpy(b0.B.view(np.uint8).copy()).pin_memory()
+    zb = sbgemm._scalar_buf(dtype, 0.0)
+    st = sbgemm.lib().sbgemm_gemm_multi_uniform_host(
+        sbgemm.TYPE_CODES[dtype], b"N", b"N", m, m, m, ctypes.addressof(ab), hA0.data_ptr(), m,
+        m * m, hB0.data_ptr(), m, m * m, ctypes.addressof(zb), hC0.data_ptr(), m, m * m, N,
+        work.data_ptr(), work.numel(), s.cuda_stream)
+    assert st == 0
+    s.synchronize()
+    got0 = hC0.numpy().view(b0.C.dtype).copy()
+    H.assert_parity(b0, got0, H.oracle_ref(b0, alpha, 0.0), alpha, 0.0)
+
+
+def test_host_array_entry_point_errors():
+    import ctypes
+    L = sbgemm.lib()
+    one = sbgemm._scalar_buf("s", 1.0)
+    work = torch.empty(64, dtype=torch.uint8, device="cuda")
+    h = torch.zeros(16 * 100, dtype=torch.float32).pin_memory()
+    # a 64-byte work buffer cannot hold two 4x4 pairs
+    st = L.sbgemm_gemm_multi_uniform_host(0, b"N", b"N", 4, 4, 4, ctypes.addressof(one), h.data_ptr(),
+                                          4, 16, h.data_ptr(), 4, 16, ctypes.addressof(one),
+                                          h.data_ptr(), 4, 16, 100, work.data_ptr(), 64, None)
+    assert st == -8
+    st = L.sbgemm_gemm_multi_uniform_host(0, b"N", b"N", 4, 4, 4, ctypes.addressof(one), h.data_ptr(),
+                                          3, 16, h.data_ptr(), 4, 16, ctypes.addressof(one),
+                                          h.data_ptr(), 4, 16, 100, work.data_ptr(), 64, None)
+    assert st == -3
