@@ -249,6 +249,42 @@ sbgemm_status sbgemm_vbatch_run(sbgemm_vplan plan, const void* alpha, const void
 sbgemm_status sbgemm_vbatch_plan_info(sbgemm_vplan plan, int* n_tiles, int* n_buckets,
                                       long long* device_bytes);
 
+/* Largest problem count sbgemm_vbatch_run_noalloc accepts. */
+#define SBGEMM_NOALLOC_MAX_PROBLEMS 262144
+
+/*
+ * The variable-size run without any memory allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * while they run, such as a plug-in inside a host application that owns all
+ * device memory, or a latency-critical loop that must keep a fixed footprint
+ * and cannot take the device-wide synchronisation cudaMalloc may imply.
+ *
+ * `problems` is a DEVICE array of `count` records (same meaning as for
+ * sbgemm_vbatch_plan_create).  The tile list, the per-problem records, the
+ * bucketing counters and the work-queue counter live in one fixed-size
+ * static device array of this library (about 13 MB, held by every GPU that
+ * loads the library until the process exits); the bucketing runs on the
+ * device, then the same persistent kernel as sbgemm_vbatch_run computes.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ *
+ *  - count above SBGEMM_NOALLOC_MAX_PROBLEMS returns SBGEMM_ERR_CAPACITY
+ *    before anything is queued.
+ *  - The first call on a device looks up the device address of the static
+ *    array (set-up, once per device, with that device current); make that
+ *    first call before any stream capture.
+ *  - Every call uses the same array: it clears the counters it needs, but
+ *    two calls whose work overlaps on the GPU (other streams, other host
+ *    threads) race on it and give wrong results.
+ *  - The tile count is read back to the host before the GEMM kernel is
+ *    launched, so the call returns after the earlier work on `stream` and
+ *    the bucketing kernels have finished.
+ *  - A problem with m, n or k outside 0..16, an op code of 3 or a negative
+ *    offset gives SBGEMM_ERR_INVALID_SIZE (no GEMM is launched).
+ */
+sbgemm_status sbgemm_vbatch_run_noalloc(int type, const sbgemm_vproblem* problems, int count,
+                                        const void* alpha, const void* A, const void* B,
+                                        const void* beta, void* C, int scalar_mode, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Timing core (autotuner).                                             */
 /* ------------------------------------------------------------------ */

@@ -50,6 +50,7 @@ SIGNATURES = {
     "sbgemm_vbatch_run": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "sbgemm_vbatch_plan_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
                                      ctypes.POINTER(_ll)]),
+    "sbgemm_vbatch_run_noalloc": (_i, [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "sbgemm_timer_create": (_i, [ctypes.POINTER(_vp), _i]),
     "sbgemm_timer_mark": (_i, [_vp, _i, _vp]),
     "sbgemm_timer_elapsed": (_i, [_vp, _i, _i, ctypes.POINTER(ctypes.c_float)]),
