@@ -157,12 +157,35 @@ sbgemm_status sbgemm_Bgemm_multi_uniform_async(char transa, char transb, int m, 
  * copies finish (synchronise the stream before reading hC).  Host scalars
  * only; lda2 and ldb2 must be nonzero.  C is copied in when beta != 0 or
  * when its layout has gaps.  Allocates nothing; SBGEMM_ERR_CAPACITY when
- * dwork cannot hold two pairs.  Calls that share dwork must be ordered.
+ * half of dwork cannot hold one pair.  Calls that share dwork must be
+ * ordered.
  */
 sbgemm_status sbgemm_gemm_multi_uniform_host(int type, char transa, char transb,
     int m, int n, int k, const void* alpha, const void* hA, int lda, long long lda2,
     const void* hB, int ldb, long long ldb2, const void* beta, void* hC, int ldc,
     long long ldc2, int batchCount, void* dwork, size_t dwork_bytes, void* stream);
+
+/* One uniform batch on host arrays, for sbgemm_gemm_grouped_host. */
+typedef struct {
+    char transa, transb;
+    int m, n, k;
+    const void* hA; int lda; long long lda2;
+    const void* hB; int ldb; long long ldb2;
+    void* hC; int ldc; long long ldc2;
+    int batchCount;
+} sbgemm_host_group;
+
+/*
+ * Several uniform batches on host arrays (same type, alpha and beta) as one
+ * continuous pipeline through `dwork`: the copy-back of one group overlaps
+ * the copy-in of the next, which separate sbgemm_gemm_multi_uniform_host
+ * calls cannot do (each is ordered after the previous one's last copy).
+ * Same rules as sbgemm_gemm_multi_uniform_host; every group is checked
+ * before anything is queued; SBGEMM_ERR_CAPACITY when half of dwork cannot
+ * hold one pair of some group.
+ */
+sbgemm_status sbgemm_gemm_grouped_host(int type, const void* alpha, const void* beta,
+    const sbgemm_host_group* groups, int ngroups, void* dwork, size_t dwork_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Kernel variants (used by the autotuner and the learned selector).   */

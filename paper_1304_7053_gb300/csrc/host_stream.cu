@@ -1,7 +1,9 @@
-// Eq. (1) on host-resident arrays: the batch streams through a caller-owned
-// device work buffer in chunks, double-buffered, with host->device copies,
-// kernels and device->host copies of consecutive chunks overlapping on three
-// streams (copy-in, the caller's stream for compute, copy-out).
+// Eq. (1) on host-resident arrays: one or more uniform batches stream through
+// a caller-owned device work buffer in chunks, double-buffered, with
+// host->device copies, kernels and device->host copies of consecutive chunks
+// overlapping on three streams (copy-in, the caller's stream for compute,
+// copy-out).  Several groups form one continuous pipeline, so the copy-back
+// tail of one group overlaps the copy-in of the next.
 #include <mutex>
 
 #include "sbgemm_launch.cuh"
@@ -67,89 +69,119 @@ bool scalar_is_zero(int type, const void* p) {
 }  // namespace
 }  // namespace sbg
 
-extern "C" sbgemm_status sbgemm_gemm_multi_uniform_host(int type, char transa, char transb,
-    int m, int n, int k, const void* alpha, const void* hA, int lda, long long lda2,
-    const void* hB, int ldb, long long ldb2, const void* beta, void* hC, int ldc,
-    long long ldc2, int batchCount, void* dwork, size_t dwork_bytes, void* stream) {
+// One continuous double-buffered pipeline over the chunks of every group.
+static sbgemm_status stream_groups(int type, const void* alpha, const void* beta,
+                                   const sbgemm_host_group* groups, int ngroups, void* dwork,
+                                   size_t dwork_bytes, cudaStream_t cs) {
     using namespace sbg;
     if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
-    if (m < 0 || n < 0 || k < 0 || m > 16 || n > 16 || k > 16 || batchCount < 0)
-        return SBGEMM_ERR_INVALID_SIZE;
-    if (batchCount == 0 || m == 0 || n == 0) return SBGEMM_SUCCESS;
-    if (!alpha || !beta || !hC || !dwork) return SBGEMM_ERR_NULL_POINTER;
-    if (lda2 == 0 || ldb2 == 0) return SBGEMM_ERR_NOT_SUPPORTED;   // shared A/B: use the device entry
-    {   // full argument check before anything is queued (a zero-pair call)
-        const sbgemm_status chk = gemm_uniform(type, transa, transb, m, n, k, alpha, hA, lda, lda2,
-                                               hB, ldb, ldb2, beta, hC, ldc, ldc2, 0,
-                                               SBGEMM_SCALARS_HOST, -1, (cudaStream_t)stream);
-        if (chk != SBGEMM_SUCCESS) return chk;
-    }
+    if (ngroups < 0) return SBGEMM_ERR_INVALID_SIZE;
+    if (ngroups > 0 && !groups) return SBGEMM_ERR_NULL_POINTER;
+    if (!alpha || !beta || !dwork) return SBGEMM_ERR_NULL_POINTER;
     const size_t es = elem_bytes(type);
     const bool beta0 = scalar_is_zero(type, beta);
-    // C is copied in when beta != 0, and also when its layout has gaps, so the
-    // copy back returns the gaps unchanged
-    const bool c_in = !beta0 || ldc != m || ldc2 != (long long)ldc * n;
-    const bool ab_in = k > 0 && !scalar_is_zero(type, alpha);
-    const size_t per = es * ((ab_in ? (size_t)(lda2 + ldb2) : 0) + (size_t)ldc2);
-    // two buffers, each with chunk * per bytes, 256-byte aligned sections
-    long long chunk = (long long)((dwork_bytes / 2) / (per + 1));
-    while (chunk > 0 && 2 * (((size_t)chunk * es * lda2 + 255) / 256 * 256 * (ab_in ? 1 : 0)
-                             + ((size_t)chunk * es * ldb2 + 255) / 256 * 256 * (ab_in ? 1 : 0)
-                             + ((size_t)chunk * es * ldc2 + 255) / 256 * 256) > dwork_bytes)
-        --chunk;
-    if (chunk < 1) return SBGEMM_ERR_CAPACITY;
-    // at least four chunks so the copies overlap, when the batch allows it
-    if (chunk > (batchCount + 3) / 4 && batchCount >= 4) chunk = (batchCount + 3) / 4;
-    const size_t secA = ab_in ? ((size_t)chunk * es * lda2 + 255) / 256 * 256 : 0;
-    const size_t secB = ab_in ? ((size_t)chunk * es * ldb2 + 255) / 256 * 256 : 0;
-    const size_t secC = ((size_t)chunk * es * ldc2 + 255) / 256 * 256;
-    const size_t bufsz = secA + secB + secC;
-
+    const bool alpha0 = scalar_is_zero(type, alpha);
+    const size_t half = dwork_bytes / 2 / 256 * 256;
+    // full argument checks and capacity before anything is queued
+    for (int g = 0; g < ngroups; ++g) {
+        const sbgemm_host_group& G = groups[g];
+        if (G.m < 0 || G.n < 0 || G.k < 0 || G.m > 16 || G.n > 16 || G.k > 16 || G.batchCount < 0)
+            return SBGEMM_ERR_INVALID_SIZE;
+        if (G.batchCount == 0 || G.m == 0 || G.n == 0) continue;
+        if (!G.hC) return SBGEMM_ERR_NULL_POINTER;
+        if (G.lda2 == 0 || G.ldb2 == 0) return SBGEMM_ERR_NOT_SUPPORTED;
+        const sbgemm_status chk = gemm_uniform(type, G.transa, G.transb, G.m, G.n, G.k, alpha,
+                                               G.hA, G.lda, G.lda2, G.hB, G.ldb, G.ldb2, beta,
+                                               G.hC, G.ldc, G.ldc2, 0, SBGEMM_SCALARS_HOST, -1, cs);
+        if (chk != SBGEMM_SUCCESS) return chk;
+        const bool ab_in = G.k > 0 && !alpha0;
+        const size_t perA = ab_in ? es * (size_t)G.lda2 : 0, perB = ab_in ? es * (size_t)G.ldb2 : 0;
+        const size_t perC = es * (size_t)G.ldc2;
+        if (3 * 256 + perA + perB + perC > half) return SBGEMM_ERR_CAPACITY;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     StreamSet* ss = nullptr;
     sbgemm_status st = stream_set(&ss);
     if (st != SBGEMM_SUCCESS) return st;
-    cudaStream_t cs = (cudaStream_t)stream;
     cudaError_t e;
     // everything earlier on the caller's stream comes first
     if ((e = cudaEventRecord(ss->start, cs)) != cudaSuccess) return (sbgemm_status)e;
     if ((e = cudaStreamWaitEvent(ss->in, ss->start, 0)) != cudaSuccess) return (sbgemm_status)e;
-    const char* a8 = static_cast<const char*>(hA);
-    const char* b8 = static_cast<const char*>(hB);
-    char* c8 = static_cast<char*>(hC);
-    int last = 0;
-    for (long long p0 = 0, i = 0; p0 < batchCount; p0 += chunk, ++i) {
-        const int b = (int)(i & 1);
-        last = b;
-        const long long cnt = (batchCount - p0) < chunk ? (batchCount - p0) : chunk;
-        char* base = static_cast<char*>(dwork) + b * bufsz;
-        char* dA = base;
-        char* dB = base + secA;
-        char* dC = base + secA + secB;
-        // spans: the last matrix of a chunk ends at its own last element
-        const size_t spanA = es * ((size_t)(cnt - 1) * lda2 + (size_t)lda * (transa == 'N' || transa == 'n' ? k : m));
-        const size_t spanB = es * ((size_t)(cnt - 1) * ldb2 + (size_t)ldb * (transb == 'N' || transb == 'n' ? n : k));
-        const size_t spanC = es * ((size_t)(cnt - 1) * ldc2 + (size_t)ldc * n);
-        if ((e = cudaStreamWaitEvent(ss->in, ss->d2h[b], 0)) != cudaSuccess) return (sbgemm_status)e;
-        if (ab_in) {
-            if ((e = cudaMemcpyAsync(dA, a8 + es * (size_t)p0 * lda2, spanA, cudaMemcpyHostToDevice, ss->in)) != cudaSuccess) return (sbgemm_status)e;
-            if ((e = cudaMemcpyAsync(dB, b8 + es * (size_t)p0 * ldb2, spanB, cudaMemcpyHostToDevice, ss->in)) != cudaSuccess) return (sbgemm_status)e;
+    long long i = 0;           // chunk counter across all groups
+    for (int g = 0; g < ngroups; ++g) {
+        const sbgemm_host_group& G = groups[g];
+        if (G.batchCount == 0 || G.m == 0 || G.n == 0) continue;
+        const int m = G.m, n = G.n, k = G.k;
+        const bool ab_in = k > 0 && !alpha0;
+        // C is copied in when beta != 0, and also when its layout has gaps,
+        // so the copy back returns the gaps unchanged
+        const bool c_in = !beta0 || G.ldc != m || G.ldc2 != (long long)G.ldc * n;
+        const size_t perA = ab_in ? es * (size_t)G.lda2 : 0, perB = ab_in ? es * (size_t)G.ldb2 : 0;
+        const size_t perC = es * (size_t)G.ldc2;
+        long long chunk = (long long)((half - 3 * 256) / (perA + perB + perC));
+        // at least four chunks per group so its copies overlap
+        if (G.batchCount >= 4 && chunk > (G.batchCount + 3) / 4) chunk = (G.batchCount + 3) / 4;
+        if (chunk < 1) chunk = 1;
+        const size_t secA = (chunk * perA + 255) / 256 * 256;
+        const size_t secB = (chunk * perB + 255) / 256 * 256;
+        const char* a8 = static_cast<const char*>(G.hA);
+        const char* b8 = static_cast<const char*>(G.hB);
+        char* c8 = static_cast<char*>(G.hC);
+        const bool na = G.transa == 'N' || G.transa == 'n', nbt = G.transb == 'N' || G.transb == 'n';
+        for (long long p0 = 0; p0 < G.batchCount; p0 += chunk, ++i) {
+            const int b = (int)(i & 1);
+            const long long cnt = (G.batchCount - p0) < chunk ? (G.batchCount - p0) : chunk;
+            char* base = static_cast<char*>(dwork) + b * half;
+            char* dA = base;
+            char* dB = base + secA;
+            char* dC = base + secA + secB;
+            // spans: the last matrix of a chunk ends at its own last element
+            const size_t spanA = es * ((size_t)(cnt - 1) * G.lda2 + (size_t)G.lda * (na ? k : m));
+            const size_t spanB = es * ((size_t)(cnt - 1) * G.ldb2 + (size_t)G.ldb * (nbt ? n : k));
+            const size_t spanC = es * ((size_t)(cnt - 1) * G.ldc2 + (size_t)G.ldc * n);
+            if ((e = cudaStreamWaitEvent(ss->in, ss->d2h[b], 0)) != cudaSuccess) return (sbgemm_status)e;
+            if (ab_in) {
+                if ((e = cudaMemcpyAsync(dA, a8 + es * (size_t)p0 * G.lda2, spanA, cudaMemcpyHostToDevice, ss->in)) != cudaSuccess) return (sbgemm_status)e;
+                if ((e = cudaMemcpyAsync(dB, b8 + es * (size_t)p0 * G.ldb2, spanB, cudaMemcpyHostToDevice, ss->in)) != cudaSuccess) return (sbgemm_status)e;
+            }
+            if (c_in && (e = cudaMemcpyAsync(dC, c8 + es * (size_t)p0 * G.ldc2, spanC, cudaMemcpyHostToDevice, ss->in)) != cudaSuccess)
+                return (sbgemm_status)e;
+            if ((e = cudaEventRecord(ss->h2d[b], ss->in)) != cudaSuccess) return (sbgemm_status)e;
+            if ((e = cudaStreamWaitEvent(cs, ss->h2d[b], 0)) != cudaSuccess) return (sbgemm_status)e;
+            st = gemm_uniform(type, G.transa, G.transb, m, n, k, alpha, dA, G.lda, G.lda2, dB, G.ldb,
+                              G.ldb2, beta, dC, G.ldc, G.ldc2, (int)cnt, SBGEMM_SCALARS_HOST, -1, cs);
+            if (st != SBGEMM_SUCCESS) return st;
+            if ((e = cudaEventRecord(ss->comp[b], cs)) != cudaSuccess) return (sbgemm_status)e;
+            if ((e = cudaStreamWaitEvent(ss->out, ss->comp[b], 0)) != cudaSuccess) return (sbgemm_status)e;
+            if ((e = cudaMemcpyAsync(c8 + es * (size_t)p0 * G.ldc2, dC, spanC, cudaMemcpyDeviceToHost, ss->out)) != cudaSuccess)
+                return (sbgemm_status)e;
+            if ((e = cudaEventRecord(ss->d2h[b], ss->out)) != cudaSuccess) return (sbgemm_status)e;
         }
-        if (c_in && (e = cudaMemcpyAsync(dC, c8 + es * (size_t)p0 * ldc2, spanC, cudaMemcpyHostToDevice, ss->in)) != cudaSuccess)
-            return (sbgemm_status)e;
-        if ((e = cudaEventRecord(ss->h2d[b], ss->in)) != cudaSuccess) return (sbgemm_status)e;
-        if ((e = cudaStreamWaitEvent(cs, ss->h2d[b], 0)) != cudaSuccess) return (sbgemm_status)e;
-        st = gemm_uniform(type, transa, transb, m, n, k, alpha, dA, lda, lda2, dB, ldb, ldb2, beta,
-                          dC, ldc, ldc2, (int)cnt, SBGEMM_SCALARS_HOST, -1, cs);
-        if (st != SBGEMM_SUCCESS) return st;
-        if ((e = cudaEventRecord(ss->comp[b], cs)) != cudaSuccess) return (sbgemm_status)e;
-        if ((e = cudaStreamWaitEvent(ss->out, ss->comp[b], 0)) != cudaSuccess) return (sbgemm_status)e;
-        if ((e = cudaMemcpyAsync(c8 + es * (size_t)p0 * ldc2, dC, spanC, cudaMemcpyDeviceToHost, ss->out)) != cudaSuccess)
-            return (sbgemm_status)e;
-        if ((e = cudaEventRecord(ss->d2h[b], ss->out)) != cudaSuccess) return (sbgemm_status)e;
     }
-    // the caller's stream continues after the last copy back
-    if ((e = cudaStreamWaitEvent(cs, ss->d2h[last], 0)) != cudaSuccess) return (sbgemm_status)e;
-    if ((e = cudaStreamWaitEvent(cs, ss->d2h[last ^ 1], 0)) != cudaSuccess) return (sbgemm_status)e;
+    // the caller's stream continues after the last copies back
+    if ((e = cudaStreamWaitEvent(cs, ss->d2h[0], 0)) != cudaSuccess) return (sbgemm_status)e;
+    if ((e = cudaStreamWaitEvent(cs, ss->d2h[1], 0)) != cudaSuccess) return (sbgemm_status)e;
     return SBGEMM_SUCCESS;
+}
+
+extern "C" sbgemm_status sbgemm_gemm_multi_uniform_host(int type, char transa, char transb,
+    int m, int n, int k, const void* alpha, const void* hA, int lda, long long lda2,
+    const void* hB, int ldb, long long ldb2, const void* beta, void* hC, int ldc,
+    long long ldc2, int batchCount, void* dwork, size_t dwork_bytes, void* stream) {
+    sbgemm_host_group g;
+    g.transa = transa; g.transb = transb; g.m = m; g.n = n; g.k = k;
+    g.hA = hA; g.lda = lda; g.lda2 = lda2;
+    g.hB = hB; g.ldb = ldb; g.ldb2 = ldb2;
+    g.hC = hC; g.ldc = ldc; g.ldc2 = ldc2;
+    g.batchCount = batchCount;
+    if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
+    if (m < 0 || n < 0 || k < 0 || m > 16 || n > 16 || k > 16 || batchCount < 0)
+        return SBGEMM_ERR_INVALID_SIZE;
+    if (batchCount == 0 || m == 0 || n == 0) return SBGEMM_SUCCESS;
+    return stream_groups(type, alpha, beta, &g, 1, dwork, dwork_bytes, (cudaStream_t)stream);
+}
+
+extern "C" sbgemm_status sbgemm_gemm_grouped_host(int type, const void* alpha, const void* beta,
+    const sbgemm_host_group* groups, int ngroups, void* dwork, size_t dwork_bytes, void* stream) {
+    return stream_groups(type, alpha, beta, groups, ngroups, dwork, dwork_bytes, (cudaStream_t)stream);
 }

@@ -85,6 +85,13 @@ pipe_kernel(Args<typename Cf::Ty> g)
     using A = typename Cf::A;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
+    // Launched with programmatic stream serialisation: this grid may start
+    // while the previous kernel on the stream drains, so it waits for that
+    // grid's completion (and memory) before touching global memory, then
+    // lets the next launch begin its own set-up.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+
     A alpha = g.alpha, beta = g.beta;
     bool beta_zero = g.beta_zero != 0, alpha_zero = g.alpha_zero != 0;
     const bool has_cold = !beta_zero;          // smem layout fixed by the host
@@ -253,7 +260,18 @@ sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
     long long grid = (long long)num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, Cf::NT, gm.smem, r.stream>>>(a);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(Cf::NT);
+    lc.dynamicSmemBytes = gm.smem;
+    lc.stream = r.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t le = cudaLaunchKernelEx(&lc, kern, a);
+    if (le != cudaSuccess) return (sbgemm_status)le;
     return (sbgemm_status)cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sbgemm_Hgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
     "sbgemm_Bgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
     "sbgemm_gemm_multi_uniform_host": (_i, [_i] + _UNIFORM + [_vp, ctypes.c_size_t, _vp]),
+    "sbgemm_gemm_grouped_host": (_i, [_i, _vp, _vp, _vp, _i, _vp, ctypes.c_size_t, _vp]),
     "sbgemm_num_variants": (_i, [_i, _i, _i, _i]),
     "sbgemm_variant_name": (ctypes.c_char_p, [_i, _i, _i, _i, _i]),
     "sbgemm_gemm_multi_uniform_variant": (_i, [_i] + _UNIFORM + [_i, _i, _vp]),
@@ -244,6 +245,16 @@ def vproblems_from_desc(desc):
         out[f] = desc[:, i].astype(np.int32)
     out["a"], out["b"], out["c"] = desc[:, 4], desc[:, 5], desc[:, 6]
     return out
+
+
+class HostGroup(ctypes.Structure):
+    """``sbgemm_host_group``: one uniform batch on host arrays."""
+    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char),
+                ("m", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int),
+                ("hA", ctypes.c_void_p), ("lda", ctypes.c_int), ("lda2", ctypes.c_longlong),
+                ("hB", ctypes.c_void_p), ("ldb", ctypes.c_int), ("ldb2", ctypes.c_longlong),
+                ("hC", ctypes.c_void_p), ("ldc", ctypes.c_int), ("ldc2", ctypes.c_longlong),
+                ("batchCount", ctypes.c_int)]
 
 
 class VPlan:

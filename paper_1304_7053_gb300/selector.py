@@ -89,7 +89,8 @@ def device_name() -> str:
 class Tuner:
     """Times every variant of a problem class on the current GPU."""
 
-    def __init__(self, db: TimingDB, reps: int = 5, flush_bytes: int = 256 << 20):
+    def __init__(self, db: TimingDB, reps: int = 5, flush_bytes: int = 256 << 20,
+                 max_bytes: int = 16 * 256 * 1_000_000):
         import torch
         self.torch = torch
         self.db = db
@@ -98,16 +99,22 @@ class Tuner:
         self.flush = torch.empty(flush_bytes, dtype=torch.uint8, device=self.dev)
         self.stream = torch.cuda.current_stream(self.dev)
         self.name = device_name()
+        # one set of operand buffers for every class (uniform[-1, 1) fp32
+        # values; timing does not depend on the values)
+        g = torch.Generator(device=self.dev)
+        g.manual_seed(3)
+        n = (max_bytes + 3) // 4
+        self.pool = [torch.rand(n, device=self.dev, generator=g) * 2 - 1 for _ in range(3)]
+        self.max_bytes = max_bytes
 
     def _buffers(self, dtype, m, n, k, ta, tb, N):
-        torch = self.torch
         ar, ac = inputs.stored_shape("T" if ta else "N", m, k)
         br, bc = inputs.stored_shape("T" if tb else "N", k, n)
-        dt = getattr(torch, TORCH_DT[dtype])
-        mult = 2 if dtype in "cz" else 1
-        mk = lambda cnt: (torch.rand(max(1, cnt * mult), device=self.dev, dtype=torch.float32) * 2 - 1).to(dt)
-        return (mk(ar * ac * N), mk(br * bc * N), mk(m * n * N)), (max(1, ar), ar * ac,
-                                                                 max(1, br), br * bc, max(1, m), m * n)
+        es = inputs.ELEM_BYTES[dtype]
+        need = es * N * max(ar * ac, br * bc, m * n)
+        if need > self.max_bytes:
+            raise ValueError("problem class larger than the tuner's buffers")
+        return tuple(self.pool), (max(1, ar), ar * ac, max(1, br), br * bc, max(1, m), m * n)
 
     def time_class(self, dtype, m, n, k, ta, tb, conj, beta0, N) -> list[float]:
         """Median ms of every variant; cached in (and read from) the DB."""
@@ -281,7 +288,87 @@ def regret(times: np.ndarray, chosen: np.ndarray) -> np.ndarray:
     return times[np.arange(times.shape[0]), chosen] / best - 1.0
 
 
+def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=3, steps=3000, db_path=None,
+             dtypes=("s", "d", "c", "z", "h", "b"), install_choices=False, log=print):
+    """Collect autotuner timings for random problem classes until about
+    `n_train_timings` (class, variant) rows exist for training, time every
+    variant of `n_test` held-out classes, train the network, and report its
+    selection regret against the exhaustive choice and the default variant."""
+    import time as _time
+    t0 = _time.time()
+    db = TimingDB(db_path)
+    tuner = Tuner(db, reps=reps)
+    train, count, i = [], 0, 0
+    pool = random_classes(4 * n_train_timings, seed, dtypes)
+    while count < n_train_timings and i < len(pool):
+        c = pool[i]
+        i += 1
+        train.append(c)
+        count += sbgemm.num_variants(c[0], c[1], c[2], c[3])
+    test = random_classes(n_test, seed + 1, dtypes)
+
+    def table(classes):
+        F = np.stack([features(*c) for c in classes])
+        T = np.full((len(classes), NVAR), np.nan)
+        nv = np.zeros(len(classes), dtype=np.int64)
+        for j, c in enumerate(classes):
+            t = tuner.time_class(*c)
+            T[j, :len(t)] = t
+            nv[j] = len(t)
+        return F, T, nv
+
+    Ftr, Ttr, nvtr = table(train)
+    t1 = _time.time()
+    Fte, Tte, nvte = table(test)
+    t2 = _time.time()
+    net = CostModel(seed=seed)
+    hist = net.fit(Ftr, Ttr, steps=steps)
+    t3 = _time.time()
+    chosen = net.choose(Fte, nvte)
+    r_mlp = regret(Tte, chosen)
+    r_def = regret(Tte, np.zeros(len(test), dtype=np.int64))
+    multi = nvte > 1
+    rep = {
+        "device": tuner.name,
+        "train_classes": len(train), "train_timings": int(np.isfinite(Ttr).sum()),
+        "test_classes": len(test), "test_timings": int(np.isfinite(Tte).sum()),
+        "test_classes_with_choice": int(multi.sum()),
+        "loss_first": hist[0], "loss_last": hist[-1], "train_steps": steps,
+        "regret_mlp_mean": float(r_mlp.mean()), "regret_mlp_median": float(np.median(r_mlp)),
+        "regret_mlp_p90": float(np.percentile(r_mlp, 90)),
+        "regret_default_mean": float(r_def.mean()), "regret_default_median": float(np.median(r_def)),
+        "regret_default_p90": float(np.percentile(r_def, 90)),
+        "regret_mlp_mean_multi": float(r_mlp[multi].mean()) if multi.any() else 0.0,
+        "regret_default_mean_multi": float(r_def[multi].mean()) if multi.any() else 0.0,
+        "mlp_picks_best": float((r_mlp == 0).mean()),
+        "default_is_best": float((r_def == 0).mean()),
+        "time_mlp_total_ms": float(Tte[np.arange(len(test)), chosen].sum()),
+        "time_default_total_ms": float(Tte[:, 0].sum()),
+        "time_exhaustive_total_ms": float(np.nanmin(Tte, axis=1).sum()),
+        "seconds": {"tune_train": round(t1 - t0, 1), "tune_test": round(t2 - t1, 1),
+                    "train_network": round(t3 - t2, 1)},
+    }
+    if install_choices:
+        install(test, chosen)
+    log(json.dumps(rep))
+    return rep, net
+
+
 def install(classes, choices) -> None:
     """Write choices into the library's selection table."""
     for (dtype, m, n, k, ta, tb, conj, beta0, N), v in zip(classes, choices):
         sbgemm.set_choice(dtype, m, n, k, ta, tb, beta0, size_class(N), int(v))
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-timings", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=500)
+    ap.add_argument("--db", default=None)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    rep, _ = evaluate(a.train_timings, a.test, db_path=a.db)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(rep, f, indent=1)

@@ -1,0 +1,171 @@
+"""Throughput sweeps on the current GPU (timings only; correctness is the
+tests' job).
+
+Every timing is the median of `reps` calls, each preceded by an overwrite of
+a buffer larger than L2 so every call starts cold, measured with CUDA events
+(the library's timing core for this library's kernels).  The comparator is
+cuBLAS strided-batched GEMM through torch.bmm on the same column-major data
+(C = A B column-major is C^T = B^T A^T row-major).
+
+    python -m paper_1304_7053_gb300.sweep --out sweep.json [--quick]
+
+Sections: the fixed-size sweep (S/D/C/Z, m = 1..16, N = 1e3/1e5/1e6,
+op N/N, alpha = 1.5, beta in {0, -0.5}), the op sweep (complex single, all 9
+op pairs at N = 1e5), FEM-like rectangular shapes (S/D, N = 5e5, op(A) = T,
+beta = 1), and 16-bit storage (binary16/bfloat16, m in {8, 12, 16},
+N = 1e6).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import sys
+
+import numpy as np
+
+from . import sbgemm
+
+ES = {"s": 4, "d": 8, "c": 8, "z": 16, "h": 2, "b": 2}
+CPLX = {"c", "z"}
+
+
+class Pools:
+    """Reusable device buffers filled once with uniform[-1, 1) fp32 values
+    (other types read the same bytes; timing does not depend on values)."""
+
+    def __init__(self, max_bytes, dev):
+        import torch
+        self.torch = torch
+        n = (max_bytes + 3) // 4
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        self.A = torch.rand(n, device=dev, generator=g) * 2 - 1
+        self.B = torch.rand(n, device=dev, generator=g) * 2 - 1
+        self.C = torch.rand(n, device=dev, generator=g) * 2 - 1
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def as_dtype(self, buf, dtype):
+        torch = self.torch
+        t = {"s": torch.float32, "d": torch.float64, "c": torch.complex64,
+             "z": torch.complex128, "h": torch.float16, "b": torch.bfloat16}[dtype]
+        if dtype in ("h", "b"):
+            return buf.view(torch.int16).view(t)
+        return buf.view(t)
+
+
+def time_ours(pools, dtype, ta, tb, m, n, k, N, alpha, beta, reps, variant=None):
+    opa, opb = ta, tb
+    ar, ac = (m, k) if opa == "N" else (k, m)
+    br, bc = (k, n) if opb == "N" else (n, k)
+    L = sbgemm.lib()
+    ab, bb = sbgemm._scalar_buf(dtype, alpha), sbgemm._scalar_buf(dtype, beta)
+    if variant is None:
+        variant = sbgemm.get_choice(dtype, m, n, k, opa != "N", opb != "N", complex(beta) == 0,
+                                    size_class(N))
+    ms = ctypes.c_float()
+    s = pools.torch.cuda.current_stream().cuda_stream
+    st = L.sbgemm_time_variant(sbgemm.TYPE_CODES[dtype], opa.encode(), opb.encode(), m, n, k,
+                               ctypes.addressof(ab), pools.A.data_ptr(), max(1, ar), ar * ac,
+                               pools.B.data_ptr(), max(1, br), br * bc, ctypes.addressof(bb),
+                               pools.C.data_ptr(), max(1, m), m * n, N, variant, reps,
+                               pools.flush.data_ptr(), pools.flush.numel(), s, ctypes.byref(ms))
+    if st != 0:
+        raise sbgemm.SbgemmError(st, "time_variant")
+    return float(ms.value)
+
+
+def time_cublas(pools, dtype, m, n, k, N, reps):
+    """cuBLAS strided batched (torch.bmm) on column-major N/N data, beta = 0."""
+    torch = pools.torch
+    A = pools.as_dtype(pools.A, dtype)[:N * m * k].view(N, k, m)   # row-major view of A^T
+    B = pools.as_dtype(pools.B, dtype)[:N * k * n].view(N, n, k)   # row-major view of B^T
+    C = pools.as_dtype(pools.C, dtype)[:N * m * n].view(N, n, m)   # row-major view of C^T
+    ts = []
+    for _ in range(reps + 1):
+        pools.flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.bmm(B, A, out=C)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts = sorted(ts[1:])
+    return ts[len(ts) // 2]
+
+
+def size_class(N):
+    c = 0
+    while N >= 10 and c < 7:
+        N //= 10
+        c += 1
+    return c
+
+
+def row(dtype, ta, tb, m, n, k, N, beta, ms, cublas_ms=None):
+    es = ES[dtype]
+    fl = (8 if dtype in CPLX else 2) * m * n * k * N
+    by = es * N * (m * k + k * n + m * n * (1 + (complex(beta) != 0)))
+    r = {"dtype": dtype, "op": ta + tb, "m": m, "n": n, "k": k, "N": N, "beta": str(beta),
+         "ms": round(ms, 5), "gflops": round(fl / (ms * 1e-3) / 1e9, 1),
+         "gbps": round(by / (ms * 1e-3) / 1e9, 1)}
+    if cublas_ms is not None:
+        r["cublas_ms"] = round(cublas_ms, 5)
+        r["speedup_vs_cublas"] = round(cublas_ms / ms, 2)
+    return r
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="sweep.json")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
+    args = ap.parse_args(argv)
+    import torch
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    rows = []
+    Ns = [100_000] if args.quick else [1_000, 100_000, 1_000_000]
+    sizes = [2, 4, 8, 10, 12, 16] if args.quick else list(range(1, 17))
+    pools = Pools(16 * 256 * 1_000_000 + 4096, dev)
+
+    def emit(r, section):
+        r["section"] = section
+        rows.append(r)
+        print(json.dumps(r), flush=True)
+
+    # fixed-size sweep, op N/N
+    for dtype in ("s", "d", "c", "z"):
+        for N in Ns:
+            for m in sizes:
+                for beta in (0.0, -0.5):
+                    alpha = 1.5
+                    ms = time_ours(pools, dtype, "N", "N", m, m, m, N, alpha, beta, args.reps)
+                    cb = time_cublas(pools, dtype, m, m, m, N, args.reps) if beta == 0.0 else None
+                    emit(row(dtype, "N", "N", m, m, m, N, beta, ms, cb), "fixed")
+    # op sweep: complex single, N = 1e5, general alpha/beta
+    for m in sizes:
+        for ta in "NTC":
+            for tb in "NTC":
+                ms = time_ours(pools, "c", ta, tb, m, m, m, 100_000, 1.5 - 0.5j, -0.5 + 0.25j, args.reps)
+                emit(row("c", ta, tb, m, m, m, 100_000, -0.5, ms), "ops")
+    # FEM-like rectangular shapes
+    for dtype in ("s", "d"):
+        for (m, n, k) in ((4, 16, 4), (9, 16, 9), (16, 8, 16), (3, 9, 3), (16, 16, 1)):
+            ms = time_ours(pools, dtype, "T", "N", m, n, k, 500_000, 1.0, 1.0, args.reps)
+            emit(row(dtype, "T", "N", m, n, k, 500_000, 1.0, ms), "fem")
+    # 16-bit storage
+    for dtype in ("h", "b"):
+        for m in (8, 12, 16):
+            for beta in (0.0, -0.5):
+                ms = time_ours(pools, dtype, "N", "N", m, m, m, 1_000_000, 1.5, beta, args.reps)
+                cb = time_cublas(pools, dtype, m, m, m, 1_000_000, args.reps) if beta == 0.0 else None
+                emit(row(dtype, "N", "N", m, m, m, 1_000_000, beta, ms, cb), "16bit")
+    with open(args.out, "w") as f:
+        json.dump(rows, f)
+    return rows
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -326,3 +326,34 @@ def test_host_array_entry_point_errors():
                                           3, 16, h.data_ptr(), 4, 16, ctypes.addressof(one),
                                           h.data_ptr(), 4, 16, 100, work.data_ptr(), 64, None)
     assert st == -3
+
+
+def test_grouped_host_entry_point():
+    """Several uniform batches (different shapes and ops) as one grouped
+    host-array call through a small work buffer."""
+    import ctypes
+    specs = [("N", "N", 3, 3, 3, 5001), ("T", "N", 16, 16, 16, 2000), ("N", "T", 7, 5, 9, 3333),
+             ("C", "N", 1, 1, 1, 10)]
+    batches, groups, keep = [], (sbgemm.HostGroup * len(specs))(), []
+    for g, (ta, tb, m, n, k, N) in zip(groups, specs):
+        b = inputs.UniformBatch("s", ta, tb, m, n, k, N, seed=m + n)
+        hA = torch.from_numpy(b.A.copy()).pin_memory()
+        hB = torch.from_numpy(b.B.copy()).pin_memory()
+        hC = torch.from_numpy(b.C.copy()).pin_memory()
+        keep += [hA, hB, hC]
+        g.transa, g.transb, g.m, g.n, g.k = ta.encode(), tb.encode(), m, n, k
+        g.hA, g.lda, g.lda2 = hA.data_ptr(), b.lda, b.lda2
+        g.hB, g.ldb, g.ldb2 = hB.data_ptr(), b.ldb, b.ldb2
+        g.hC, g.ldc, g.ldc2 = hC.data_ptr(), b.ldc, b.ldc2
+        g.batchCount = N
+        batches.append((b, hC))
+    work = torch.empty(2 << 20, dtype=torch.uint8, device="cuda")
+    ab, bb = sbgemm._scalar_buf("s", 1.5), sbgemm._scalar_buf("s", -0.5)
+    s = torch.cuda.current_stream()
+    st = sbgemm.lib().sbgemm_gemm_grouped_host(0, ctypes.addressof(ab), ctypes.addressof(bb),
+                                               ctypes.addressof(groups), len(specs), work.data_ptr(),
+                                               work.numel(), s.cuda_stream)
+    assert st == 0
+    s.synchronize()
+    for b, hC in batches:
+        H.assert_parity(b, hC.numpy().copy(), H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
