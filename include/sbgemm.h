@@ -187,6 +187,82 @@ typedef struct {
 sbgemm_status sbgemm_gemm_grouped_host(int type, const void* alpha, const void* beta,
     const sbgemm_host_group* groups, int ngroups, void* dwork, size_t dwork_bytes, void* stream);
 
+/* One uniform batch on device arrays, for sbgemm_gemm_grouped. */
+typedef struct {
+    char transa, transb;
+    int m, n, k;
+    const void* A; int lda; long long lda2;
+    const void* B; int ldb; long long ldb2;
+    void* C; int ldc; long long ldc2;
+    int batchCount;
+} sbgemm_group;
+
+/*
+ * Several independent uniform batches (same type, alpha and beta) in one
+ * call.  Groups that are square (m = n = k <= 16), op N/N, stored with
+ * minimal leading dimensions and 16-byte aligned share ONE persistent
+ * launch (up to 32 per launch): their tiles interleave, so small groups cost
+ * no launch of their own.  Other groups run as separate uniform calls on the
+ * same stream.  No group may read another group's C (they run
+ * concurrently).  Every group is checked before anything is queued; the
+ * return value is that of the first failing check or launch.
+ */
+sbgemm_status sbgemm_gemm_grouped(int type, const void* alpha, const void* beta,
+                                  const sbgemm_group* groups, int ngroups,
+                                  int scalar_mode, void* stream);
+
+/*
+ * Launch configuration of the shared persistent launch of
+ * sbgemm_gemm_grouped for one storage type: threads per block (128 or 256),
+ * bytes of one pipeline stage (4096..65536, a multiple of 1024) and pipeline
+ * depth (2..4); the block's shared memory is stages*stage_bytes +
+ * stage_bytes/2 and must stay within 220 KB.  All three zero restores the
+ * default (128, 24576, 2).  Process-wide; not synchronised with calls
+ * running concurrently on other host threads.  Invalid values give
+ * SBGEMM_ERR_INVALID_VALUE and leave the configuration unchanged.
+ */
+sbgemm_status sbgemm_grouped_config(int type, int threads, int stage_bytes, int stages);
+
+/* ------------------------------------------------------------------ */
+/* Pointer-array form (Section 4, TGEMM_multi_nounif).                 */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The same product with the batch given as arrays of matrix pointers, the
+ * cuBLAS batched interface the paper compares against (Section 4 and the
+ * cuBLAS comparison of Section 7): matrix p of A is Aarray[p], with entry
+ * (i, j) at Aarray[p][i + lda*j]; likewise B and C.  Aarray, Barray and
+ * Carray are DEVICE arrays of batchCount device pointers, owned by the
+ * caller and read by the kernel.  A and B pointers may repeat; the C
+ * matrices must not overlap one another or any A or B.  Every matrix
+ * pointer is aligned to the element size (16 bytes for complex double);
+ * a matrix with ld equal to its row count that starts 16-byte aligned is
+ * moved in 16-byte chunks, anything else element by element.  Leading
+ * dimensions, trans characters, degenerate cases, scalars and return
+ * values as for the uniform calls (ld2 does not exist here).  The typed
+ * calls take host scalars and use the legacy default stream; the
+ * type-erased call takes a scalar mode and a stream (fp32 scalars for the
+ * 16-bit types).
+ */
+sbgemm_status sbgemm_Sgemm_multi_nounif(char transa, char transb, int m, int n, int k,
+    const float* alpha, const float* const* Aarray, int lda, const float* const* Barray, int ldb,
+    const float* beta, float* const* Carray, int ldc, int batchCount);
+sbgemm_status sbgemm_Dgemm_multi_nounif(char transa, char transb, int m, int n, int k,
+    const double* alpha, const double* const* Aarray, int lda, const double* const* Barray,
+    int ldb, const double* beta, double* const* Carray, int ldc, int batchCount);
+sbgemm_status sbgemm_Cgemm_multi_nounif(char transa, char transb, int m, int n, int k,
+    const sbgemm_c32* alpha, const sbgemm_c32* const* Aarray, int lda,
+    const sbgemm_c32* const* Barray, int ldb, const sbgemm_c32* beta,
+    sbgemm_c32* const* Carray, int ldc, int batchCount);
+sbgemm_status sbgemm_Zgemm_multi_nounif(char transa, char transb, int m, int n, int k,
+    const sbgemm_c64* alpha, const sbgemm_c64* const* Aarray, int lda,
+    const sbgemm_c64* const* Barray, int ldb, const sbgemm_c64* beta,
+    sbgemm_c64* const* Carray, int ldc, int batchCount);
+sbgemm_status sbgemm_gemm_multi_nounif(int type, char transa, char transb, int m, int n, int k,
+    const void* alpha, const void* const* Aarray, int lda, const void* const* Barray, int ldb,
+    const void* beta, void* const* Carray, int ldc, int batchCount, int scalar_mode,
+    void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Kernel variants (used by the autotuner and the learned selector).   */
 /* ------------------------------------------------------------------ */

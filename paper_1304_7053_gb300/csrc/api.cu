@@ -163,9 +163,59 @@ sbgemm_status gemm_uniform(int type, char transa, char transb, int m, int n, int
     return run_typed(r);
 }
 
+// The pointer-array form (Section 4's TGEMM_multi_nounif): the same
+// checks and kernels as the 3-D layout, matrix p of each operand at the
+// p-th pointer of a device array.
+sbgemm_status gemm_nounif(int type, char transa, char transb, int m, int n, int k,
+                          const void* alpha, const void* const* Ap, int lda,
+                          const void* const* Bp, int ldb, const void* beta, void* const* Cp,
+                          int ldc, int batch, int scalar_mode, cudaStream_t stream)
+{
+    if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
+    int opa = op_code(transa), opb = op_code(transb);
+    if (opa < 0 || opb < 0) return SBGEMM_ERR_INVALID_TRANS;
+    if (m < 0 || n < 0 || k < 0 || m > 16 || n > 16 || k > 16 || batch < 0)
+        return SBGEMM_ERR_INVALID_SIZE;
+    if (scalar_mode != SBGEMM_SCALARS_HOST && scalar_mode != SBGEMM_SCALARS_DEVICE)
+        return SBGEMM_ERR_INVALID_VALUE;
+    const long long ar = opa == 0 ? m : k;
+    const long long br = opb == 0 ? k : n;
+    auto max1 = [](long long v) { return v > 1 ? v : 1LL; };
+    if (lda < max1(ar) || ldb < max1(br) || ldc < max1(m)) return SBGEMM_ERR_INVALID_LD;
+    if (batch == 0 || m == 0 || n == 0) return SBGEMM_SUCCESS;
+    if (!alpha || !beta || !Cp) return SBGEMM_ERR_NULL_POINTER;
+
+    Req r;
+    std::memset(&r, 0, sizeof r);
+    r.type = type; r.m = m; r.n = n; r.k = k;
+    const bool cplx = is_complex_type(type);
+    r.ta = opa != 0; r.tb = opb != 0;
+    r.conja = cplx && opa == 2; r.conjb = cplx && opb == 2;
+    r.Ap = Ap; r.Bp = Bp; r.Cp = Cp;
+    r.lda = lda; r.ldb = ldb; r.ldc = ldc;
+    r.lda2 = r.ldb2 = r.ldc2 = -1;     // unused in the pointer-array form
+    r.batch = batch;
+    r.scalar_mode = scalar_mode;
+    r.alpha = alpha; r.beta = beta;
+    r.stream = stream;
+    if (scalar_mode == SBGEMM_SCALARS_HOST) {
+        r.alpha_zero = host_scalar_zero(type, alpha);
+        r.beta_zero = host_scalar_zero(type, beta);
+    }
+    if (k == 0 || r.alpha_zero) return scale_typed(r);
+    if (!Ap || !Bp) return SBGEMM_ERR_NULL_POINTER;
+    int variant = lookup_choice(type, m, n, k, r.ta, r.tb,
+                                scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
+                                size_class(batch));
+    if (variant < 0 || variant >= variants_for(m, n, k)) variant = 0;
+    r.variant = internal_variant(m, n, k, variant);
+    return run_typed(r);
+}
+
 }  // namespace sbg
 
 using sbg::gemm_uniform;
+using sbg::gemm_nounif;
 
 extern "C" {
 
@@ -185,6 +235,31 @@ extern "C" {
                             ldb2, beta, C, ldc, ldc2, batchCount, scalar_mode, -1,          \
                             (cudaStream_t)stream);                                          \
     }
+
+#define SBG_NOUNIF_ENTRY(L, T, CODE)                                                        \
+    sbgemm_status sbgemm_##L##gemm_multi_nounif(char transa, char transb, int m, int n, int k,  \
+        const T* alpha, const T* const* Aarray, int lda, const T* const* Barray, int ldb,   \
+        const T* beta, T* const* Carray, int ldc, int batchCount) {                         \
+        return gemm_nounif(CODE, transa, transb, m, n, k, alpha,                            \
+                           reinterpret_cast<const void* const*>(Aarray), lda,               \
+                           reinterpret_cast<const void* const*>(Barray), ldb, beta,         \
+                           reinterpret_cast<void* const*>(Carray), ldc, batchCount,         \
+                           SBGEMM_SCALARS_HOST, (cudaStream_t)0);                           \
+    }
+
+SBG_NOUNIF_ENTRY(S, float, SBGEMM_TYPE_S)
+SBG_NOUNIF_ENTRY(D, double, SBGEMM_TYPE_D)
+SBG_NOUNIF_ENTRY(C, sbgemm_c32, SBGEMM_TYPE_C)
+SBG_NOUNIF_ENTRY(Z, sbgemm_c64, SBGEMM_TYPE_Z)
+#undef SBG_NOUNIF_ENTRY
+
+sbgemm_status sbgemm_gemm_multi_nounif(int type, char transa, char transb, int m, int n, int k,
+    const void* alpha, const void* const* Aarray, int lda, const void* const* Barray, int ldb,
+    const void* beta, void* const* Carray, int ldc, int batchCount, int scalar_mode,
+    void* stream) {
+    return gemm_nounif(type, transa, transb, m, n, k, alpha, Aarray, lda, Barray, ldb, beta,
+                       Carray, ldc, batchCount, scalar_mode, (cudaStream_t)stream);
+}
 
 SBG_PAPER_ENTRY(S, float, SBGEMM_TYPE_S)
 SBG_PAPER_ENTRY(D, double, SBGEMM_TYPE_D)
@@ -217,8 +292,9 @@ int sbgemm_num_variants(int type, int m, int n, int k) {
 
 const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
     static const char* names[] = {
-        "pipe tile16K st3 occ-max", "pipe tile8K st4 occ-max", "pipe tile32K st2 occ-max",
-        "pipe tile16K st3 1cta/sm", "pipe tile4K st4 occ-max", "pipe tile24K st3 2cta/sm",
+        "pipe tile16K st3 occ-max (st2 for fp64)", "pipe tile8K st4 occ-max",
+        "pipe tile32K st2 occ-max", "pipe tile16K st3 1cta/sm (st2 for fp64)",
+        "pipe tile4K st4 occ-max", "pipe tile24K st3 2cta/sm",
         "generic thread-per-entry"};
     const int nv = sbgemm_num_variants(type, m, n, k);
     if (variant < 0 || variant >= nv) return "invalid";

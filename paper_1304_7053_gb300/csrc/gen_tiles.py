@@ -9,7 +9,10 @@ thread a TM x TN block of C, the model counts per pair:
     addresses broadcast);
   * FMA instructions, including the duplicates of ragged tiles;
   * how many blocks fit an SM's shared memory (three pipeline stages of one
-    compute round of pairs each) and so how many warps compute at once;
+    compute round of pairs each, two for fp64 types) and so how many warps
+    compute at once;
+  * for fp64 types, the fp64 FMA pipe (2 per clock per SM), derated when
+    fewer than eight warps compute;
 and picks the configuration with the smallest
   max(issue cycles, shared-memory wavefronts)
 under a register budget for accumulators plus fragments.  Rows and columns of
@@ -36,6 +39,8 @@ TYPES = {  # code: (element bytes, complex, fma per mac, unused)
 }
 REG_LIMIT = 96                   # registers for accumulators plus fragments
 STAGES = 3                       # pipeline depth of the default variant
+FP64_TYPES = (1, 3)              # double and complex double: fp64-pipe bound, 2 stages
+FP64_FMA_PER_CLK = 2.0           # measured fp64 FMA rate per SM per clock on GB300
 SMEM_PER_SM = 227 * 1024
 ISSUE_PER_CLK = 4 * 32 * 0.7     # thread-instructions per clock per SM (4 schedulers, derated)
 
@@ -200,7 +205,8 @@ def cost(code, M, N, K, TA, TB, TM, TN, SI, SJ, NT):
     busy = min(P, MPR) / MPR            # fraction of the round's threads with work
     bpp_in = (p["SA_P"] + p["SB_P"]) * es
     out_bpp = 0 if VS else padded(M * N, es) * es
-    cta_smem = STAGES * P * bpp_in + P * out_bpp
+    stages = 2 if code in FP64_TYPES else STAGES
+    cta_smem = stages * P * bpp_in + P * out_bpp
     ctas = min(2048 // NT, SMEM_PER_SM // max(1, cta_smem))
     if ctas < 1:
         return None
@@ -211,6 +217,11 @@ def cost(code, M, N, K, TA, TB, TM, TN, SI, SJ, NT):
     issue_clk = ins_pair / 32.0 / ipc
     wf_total = wf_per_pair + epi_wf
     score = max(issue_clk, wf_total)
+    if code in FP64_TYPES:
+        # the fp64 pipe (2 FMA per clock per SM) binds; its four schedulers
+        # need enough computing warps to stay busy
+        fp64_clk = TPM * fma_thread / FP64_FMA_PER_CLK
+        score = max(score, fp64_clk / min(1.0, warps / 8.0))
     if ctas == 1:
         # one block per SM: its barrier-separated phases leave bubbles that no
         # other block fills

@@ -1,0 +1,13 @@
+// Grouped persistent kernel, storage type D.
+#include "grouped.cuh"
+
+namespace sbg {
+
+void gkinds_D(int threads, GKindInfo* out) { gkind_table<TyD>(threads, out); }
+
+sbgemm_status grun_D(const GIn* in, int n, const void* alpha, const void* beta, int scalar_mode,
+                        int beta_zero, int alpha_zero, const GConfig& cfg, cudaStream_t stream) {
+    return grouped_launch<TyD>(in, n, alpha, beta, scalar_mode, beta_zero, alpha_zero, cfg, stream);
+}
+
+}  // namespace sbg

@@ -25,6 +25,7 @@ struct StreamSet {
 
 std::mutex g_mu;
 StreamSet g_sets[64];
+constexpr size_t kChunkBytes = 48u << 20;
 
 sbgemm_status stream_set(StreamSet** out) {
     int dev = 0;
@@ -118,10 +119,13 @@ static sbgemm_status stream_groups(int type, const void* alpha, const void* beta
         const bool c_in = !beta0 || G.ldc != m || G.ldc2 != (long long)G.ldc * n;
         const size_t perA = ab_in ? es * (size_t)G.lda2 : 0, perB = ab_in ? es * (size_t)G.ldb2 : 0;
         const size_t perC = es * (size_t)G.ldc2;
-        long long chunk = (long long)((half - 3 * 256) / (perA + perB + perC));
-        // at least four chunks per group so its copies overlap
-        if (G.batchCount >= 4 && chunk > (G.batchCount + 3) / 4) chunk = (G.batchCount + 3) / 4;
+        // chunks of about kChunkBytes: large enough that a copy's fixed cost
+        // is small, small enough that copies of consecutive chunks overlap
+        // (a small group is one chunk; the pipeline runs across groups)
+        const size_t limit = half - 3 * 256 < kChunkBytes ? half - 3 * 256 : kChunkBytes;
+        long long chunk = (long long)(limit / (perA + perB + perC));
         if (chunk < 1) chunk = 1;
+        if (chunk > G.batchCount) chunk = G.batchCount;
         const size_t secA = (chunk * perA + 255) / 256 * 256;
         const size_t secB = (chunk * perB + 255) / 256 * 256;
         const char* a8 = static_cast<const char*>(G.hA);

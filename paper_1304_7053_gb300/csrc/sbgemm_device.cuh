@@ -75,11 +75,20 @@ __device__ __forceinline__ void mac(double2& c, double2 a, double2 b) {
     c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
 }
 
-// imaginary-part sign for conjugation (identity for real types)
+// Conjugation (Section 5 "conjugate" functor): the imaginary part's sign
+// bit is flipped when s is -1.  The flip is an integer XOR, so it costs no
+// floating-point pipe slot (the fp64 pipe is the bound for complex double).
+// Identity for real types.
 __device__ __forceinline__ float   conj_s(float a, float)     { return a; }
 __device__ __forceinline__ double  conj_s(double a, double)   { return a; }
-__device__ __forceinline__ float2  conj_s(float2 a, float s)  { return make_float2(a.x, a.y * s); }
-__device__ __forceinline__ double2 conj_s(double2 a, double s){ return make_double2(a.x, a.y * s); }
+__device__ __forceinline__ float2  conj_s(float2 a, float s) {
+    const unsigned m = __float_as_uint(s) & 0x80000000u;
+    return make_float2(a.x, __uint_as_float(__float_as_uint(a.y) ^ m));
+}
+__device__ __forceinline__ double2 conj_s(double2 a, double s) {
+    const unsigned long long m = (unsigned long long)__double_as_longlong(s) & 0x8000000000000000ull;
+    return make_double2(a.x, __longlong_as_double((long long)((unsigned long long)__double_as_longlong(a.y) ^ m)));
+}
 
 // alpha * x
 __device__ __forceinline__ float   mul(float a, float x)     { return a * x; }
@@ -149,6 +158,10 @@ struct Args {
     const A* beta_ptr;
     typename Ty::R conja, conjb; // +1 or -1: sign applied to imaginary parts
     int flat;                    // bit 0: A flat, bit 1: B flat, bit 2: C flat
+    int shared;                  // bit 0: one A for every pair (lda2 == 0), bit 1: one B (ldb2 == 0)
+    // pointer-array form (Section 4's TGEMM_multi_nounif): matrix p of X at
+    // Xp[p] with leading dimension ldx; null for the uniform 3-D layout
+    const S* const* Ap; const S* const* Bp; S* const* Cp;
     int beta_zero;               // host mode: beta == 0 known on the host
     int alpha_zero;              // host mode: alpha == 0 known on the host
     int P;                       // pairs per tile
@@ -161,6 +174,9 @@ struct Args {
 __host__ __device__ constexpr int padded_elems(int elems, int es) {
     return ((elems * es) % 16 == 0 && ((elems * es) / 16) % 2 == 0) ? elems + 16 / es : elems;
 }
+
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b ? gcd_c(b, a % b) : a; }
+__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
 
 // Largest vector (elements, at most 16 bytes) dividing a, b and c.
 __host__ __device__ constexpr int pick_vec(int es, int a, int b, int c) {
@@ -224,7 +240,7 @@ __device__ __forceinline__ void stage_operand(S* sdst, const S* g, long long ld2
         char* dst = reinterpret_cast<char*>(sdst);
         const int nbytes = cnt * SE * ES;
         const int nfull = nbytes >> 4;
-        if (SP == SE) {
+        if constexpr (SP == SE) {
 #pragma unroll 4
             for (int c = tid; c < nfull; c += NT) cp_async16(dst + 16 * c, src + 16 * c, 16);
         } else {
@@ -264,7 +280,7 @@ __device__ __forceinline__ void store_operand(S* g, const S* ssrc, long long ld2
         const char* src = reinterpret_cast<const char*>(ssrc);
         const int nbytes = cnt * SE * ES;
         const int nfull = nbytes >> 4;
-        if (SP == SE) {
+        if constexpr (SP == SE) {
 #pragma unroll 4
             for (int c = tid; c < nfull; c += NT)
                 *reinterpret_cast<uint4*>(dst + 16 * c) = *reinterpret_cast<const uint4*>(src + 16 * c);
@@ -294,6 +310,85 @@ __device__ __forceinline__ void store_operand(S* g, const S* ssrc, long long ld2
             const int row = r % ROWS, col = r / ROWS;
             g[(p0 + q) * ld2 + row + (long long)col * ld] = ssrc[q * SP + r];
         }
+    }
+}
+
+// One pointer from a read-only device array, through the non-coherent
+// (read-only) cache path.
+template <class P>
+__device__ __forceinline__ P ldg_ptr(const P* a) {
+    return reinterpret_cast<P>(__ldg(reinterpret_cast<const unsigned long long*>(a)));
+}
+
+// Pointer-array staging: matrix p0+q at ptrs[p0+q] with leading dimension
+// ld.  A matrix stored contiguously (ld == ROWS) whose start is 16-byte
+// aligned moves in 16-byte chunks; anything else moves element by element.
+template <class S, int SE, int SP, int ROWS, int NT>
+__device__ __forceinline__ void stage_ptrs(S* sdst, const S* const* ptrs, int ld, long long p0,
+                                           int cnt)
+{
+    constexpr int ES = sizeof(S);
+    const int tid = threadIdx.x;
+    if constexpr ((SE * ES) % 16 == 0) {
+        if (ld == ROWS) {
+            constexpr int CPM = SE * ES / 16;
+            constexpr int EPC = 16 / ES;
+            for (int c = tid; c < cnt * CPM; c += NT) {
+                const int q = c / CPM, r = c - q * CPM;
+                const S* src = ldg_ptr(ptrs + p0 + q) + r * EPC;
+                S* dst = sdst + q * SP + r * EPC;
+                if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                    cp_async16(dst, src, 16);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < EPC; ++v) {
+                        if constexpr (ES == 4 || ES == 8 || ES == 16) cp_async_elem<ES>(dst + v, src + v);
+                        else dst[v] = src[v];
+                    }
+                }
+            }
+            return;
+        }
+    }
+    for (int e = tid; e < cnt * SE; e += NT) {
+        const int q = e / SE, r = e - q * SE;
+        const int row = r % ROWS, col = r / ROWS;
+        const S* src = ldg_ptr(ptrs + p0 + q) + row + (long long)col * ld;
+        S* dst = sdst + q * SP + r;
+        if constexpr (ES == 4 || ES == 8 || ES == 16) cp_async_elem<ES>(dst, src);
+        else *dst = *src;
+    }
+}
+
+// Write cnt result matrices (slot stride SP) through a pointer array.
+template <class S, int SE, int SP, int ROWS, int NT>
+__device__ __forceinline__ void store_ptrs(S* const* ptrs, const S* ssrc, int ld, long long p0,
+                                           int cnt)
+{
+    constexpr int ES = sizeof(S);
+    const int tid = threadIdx.x;
+    if constexpr ((SE * ES) % 16 == 0) {
+        if (ld == ROWS) {
+            constexpr int CPM = SE * ES / 16;
+            constexpr int EPC = 16 / ES;
+            for (int c = tid; c < cnt * CPM; c += NT) {
+                const int q = c / CPM, r = c - q * CPM;
+                S* dst = ldg_ptr(ptrs + p0 + q) + r * EPC;
+                const S* src = ssrc + q * SP + r * EPC;
+                if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < EPC; ++v) dst[v] = src[v];
+                }
+            }
+            return;
+        }
+    }
+    for (int e = tid; e < cnt * SE; e += NT) {
+        const int q = e / SE, r = e - q * SE;
+        const int row = r % ROWS, col = r / ROWS;
+        ldg_ptr(ptrs + p0 + q)[row + (long long)col * ld] = ssrc[q * SP + r];
     }
 }
 
@@ -349,7 +444,8 @@ __device__ __forceinline__ void stvec(S* p, const S* in) {
 // op(A)(i, l) = TA ? A[l + K i] : A[i + M l];  op(B)(l, j) = TB ? B[j + N l] : B[l + K j]
 // (Section 2 op, Section 4 layout with minimal leading dimensions).
 // direct: write C straight to gC (matrix q at gC + q*SC) with vector stores,
-// else to the shared tile sOut.
+// else to the shared tile sOut.  sh bit 0 / bit 1: every pair reads the one
+// A / B slot at sA / sB (a matrix shared by the whole batch).
 template <class Cf>
 __device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__ sA,
                                               const typename Cf::S* __restrict__ sB,
@@ -359,14 +455,15 @@ __device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__
                                               int q, int ti, int tj,
                                               typename Cf::A alpha, typename Cf::A beta,
                                               bool beta_zero, bool alpha_one, bool skip_ab,
-                                              typename Cf::R conja, typename Cf::R conjb)
+                                              typename Cf::R conja, typename Cf::R conjb,
+                                              int sh = 0)
 {
     using S = typename Cf::S;
     using A = typename Cf::A;
     constexpr int M = Cf::M, N = Cf::N, K = Cf::K, TM = Cf::TM, TN = Cf::TN;
     constexpr int TI = Cf::TI, TJ = Cf::TJ, VL = Cf::VL, VI = Cf::VI, VJ = Cf::VJ;
-    const S* a = sA + q * Cf::SA_P;
-    const S* b = sB + q * Cf::SB_P;
+    const S* a = sA + ((sh & 1) ? 0 : q * Cf::SA_P);
+    const S* b = sB + ((sh & 2) ? 0 : q * Cf::SB_P);
 
     int ri[TM], cj[TN];   // clamped row / column of each block entry
 #pragma unroll

@@ -24,6 +24,9 @@ struct Req {
     int alpha_zero;
     int variant;
     cudaStream_t stream;
+    // pointer-array form: device arrays of per-pair matrix pointers (the
+    // 3-D layout fields A, B, C and the ld2 strides are then unused)
+    const void* const* Ap; const void* const* Bp; void* const* Cp;
 };
 
 // Run-time launch options that do not change the kernel binary.
@@ -37,14 +40,17 @@ struct LaunchOpts {
 // shape is the generic runtime-size kernel (one thread per C entry, the
 // mapping of the paper's first method in Section 6).
 constexpr int kNumPipeVariants = 6;
-inline LaunchOpts pipe_variant(int v) {
+inline LaunchOpts pipe_variant(int v, int type_code = 0) {
+    // fp64 types are bound by the fp64 pipe, not by memory: two stages are
+    // enough and leave room for more computing warps
+    const bool fp64 = type_code == 1 || type_code == 3;
     switch (v) {
     case 1:  return {8192, 4, 0};
     case 2:  return {32768, 2, 0};
-    case 3:  return {16384, 3, 1};
+    case 3:  return {16384, fp64 ? 2 : 3, 1};
     case 4:  return {4096, 4, 0};
     case 5:  return {24576, 3, 2};
-    default: return {16384, 3, 0};
+    default: return {16384, fp64 ? 2 : 3, 0};
     }
 }
 
@@ -73,6 +79,29 @@ inline void fill_args(Args<Ty>& a, const Req& r) {
     }
     a.conja = r.conja ? typename Ty::R(-1) : typename Ty::R(1);
     a.conjb = r.conjb ? typename Ty::R(-1) : typename Ty::R(1);
+    a.Ap = reinterpret_cast<const S* const*>(r.Ap);
+    a.Bp = reinterpret_cast<const S* const*>(r.Bp);
+    a.Cp = reinterpret_cast<S* const*>(r.Cp);
+    a.shared = r.Cp ? 0 : (r.lda2 == 0 ? 1 : 0) | (r.ldb2 == 0 ? 2 : 0);
+    a.flat = 0;
+}
+
+// Base of matrix p of an operand: pointer-array form or 3-D layout.
+template <class S>
+__device__ __forceinline__ const S* mat_of(const S* base, const S* const* ptrs, long long ld2,
+                                           long long p) {
+    return ptrs ? ldg_ptr(ptrs + p) : base + p * ld2;
+}
+template <class S>
+__device__ __forceinline__ S* mat_of(S* base, S* const* ptrs, long long ld2, long long p) {
+    return ptrs ? ldg_ptr(ptrs + p) : base + p * ld2;
+}
+
+// Shared-memory elements reserved for one shared (broadcast) matrix slot,
+// rounded up to 16 bytes so the slot after it stays vector-aligned.
+template <class S>
+__host__ __device__ constexpr int shared_slot_elems(int slot_elems) {
+    return (int)(((size_t)slot_elems * sizeof(S) + 15) / 16 * 16 / sizeof(S));
 }
 
 // ------------------------------------------------------------ pipelined kernel
@@ -102,27 +131,51 @@ pipe_kernel(Args<typename Cf::Ty> g)
 
     const int P = g.P;
     const int stages = g.stages;
-    const int stage_elems = P * (Cf::SA_P + Cf::SB_P + (has_cold ? Cf::SC_P : 0));
-    S* stage_base = reinterpret_cast<S*>(smem_raw);
-    S* sOut = stage_base + stages * stage_elems;    // unused when C is stored directly
-
     const long long batch = g.batch;
     const int ntiles = (int)((batch + P - 1) / P);
     const bool fa = g.flat & 1, fb = g.flat & 2, fc = g.flat & 4;
     const bool direct = (Cf::VS > 0) && fc;
+    // A matrix shared by every pair (leading dimension 2 of zero) is staged
+    // once per block into its own slot and left out of the tiles.
+    const int sh = g.shared;
+    const bool shA = sh & 1, shB = sh & 2;
+    const int offB = shA ? 0 : P * Cf::SA_P;
+    const int offC = offB + (shB ? 0 : P * Cf::SB_P);
+    const int stage_elems = offC + (has_cold ? P * Cf::SC_P : 0);
+    S* stage_base = reinterpret_cast<S*>(smem_raw);
+    S* sOut = stage_base + stages * stage_elems;    // unused when C is stored directly
+    S* sShA = sOut + (direct ? 0 : P * Cf::SC_P);
+    S* sShB = sShA + (shA ? shared_slot_elems<S>(Cf::SA_P) : 0);
 
+    const bool ptr_form = g.Cp != nullptr;
     auto issue = [&](int t, int s) {
         S* st = stage_base + s * stage_elems;
         const long long p0 = (long long)t * P;
         const int cnt = (int)min((long long)P, batch - p0);
+        if (ptr_form) {
+            if (!skip_ab) {
+                stage_ptrs<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.Ap, g.lda, p0, cnt);
+                stage_ptrs<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + offB, g.Bp, g.ldb, p0, cnt);
+            }
+            if (!beta_zero)
+                stage_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, g.Cp, g.ldc, p0, cnt);
+            return;
+        }
         if (!skip_ab) {
-            stage_operand<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.A_, g.lda2, g.lda, p0, cnt, fa);
-            stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + P * Cf::SA_P, g.B_, g.ldb2, g.ldb, p0, cnt, fb);
+            if (!shA)
+                stage_operand<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.A_, g.lda2, g.lda, p0, cnt, fa);
+            if (!shB)
+                stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + offB, g.B_, g.ldb2, g.ldb, p0, cnt, fb);
         }
         if (!beta_zero)
-            stage_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + P * (Cf::SA_P + Cf::SB_P), g.C_,
-                                                              g.ldc2, g.ldc, p0, cnt, fc);
+            stage_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, g.C_, g.ldc2, g.ldc, p0, cnt, fc);
     };
+
+    // the shared matrices join the first commit group
+    if (!skip_ab && (int)blockIdx.x < ntiles) {
+        if (shA) stage_operand<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(sShA, g.A_, 0, g.lda, 0, 1, false);
+        if (shB) stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(sShB, g.B_, 0, g.ldb, 0, 1, false);
+    }
 
     for (int s = 0; s < stages - 1; ++s) {
         const int t = blockIdx.x + s * gridDim.x;
@@ -149,14 +202,17 @@ pipe_kernel(Args<typename Cf::Ty> g)
         const int cnt = (int)min((long long)P, batch - p0);
         S* gC = g.C_ + p0 * Cf::SC;
         if (active) {
+            const S* sA = shA ? sShA : st;
+            const S* sB = shB ? sShB : st + offB;
             for (int q = ql; q < cnt; q += Cf::MPR)
-                compute_block<Cf>(st, st + P * Cf::SA_P, st + P * (Cf::SA_P + Cf::SB_P), sOut,
-                                  gC, direct, q, ti, tj, alpha, beta, beta_zero, alpha_one,
-                                  skip_ab, g.conja, g.conjb);
+                compute_block<Cf>(sA, sB, st + offC, sOut, gC, direct, q, ti, tj, alpha, beta,
+                                  beta_zero, alpha_one, skip_ab, g.conja, g.conjb, sh);
         }
         // every thread is done reading this stage before it is refilled
         __syncthreads();
-        if (!direct)
+        if (ptr_form)
+            store_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.Cp, sOut, g.ldc, p0, cnt);
+        else if (!direct)
             store_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.C_, sOut, g.ldc2, g.ldc, p0, cnt, fc);
     }
     cp_async_wait_dyn(0);
@@ -175,16 +231,22 @@ inline int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 struct Geom { int P; size_t smem; };
 
 template <class Cf>
-inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool direct) {
+inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool direct,
+                      int shared = 0) {
+    using S = typename Cf::S;
     constexpr int ES = Cf::ES;
+    const bool shA = shared & 1, shB = shared & 2;
     int quantum = 1;
-    quantum = lcm_i(quantum, 16 / gcd_i(Cf::SA * ES, 16));
-    quantum = lcm_i(quantum, 16 / gcd_i(Cf::SB * ES, 16));
+    if (!shA) quantum = lcm_i(quantum, 16 / gcd_i(Cf::SA * ES, 16));
+    if (!shB) quantum = lcm_i(quantum, 16 / gcd_i(Cf::SB * ES, 16));
     quantum = lcm_i(quantum, 16 / gcd_i(Cf::SC * ES, 16));
-    const size_t in_bpp = (size_t)(Cf::SA_P + Cf::SB_P + (has_cold ? Cf::SC_P : 0)) * ES;
+    const size_t in_bpp =
+        (size_t)((shA ? 0 : Cf::SA_P) + (shB ? 0 : Cf::SB_P) + (has_cold ? Cf::SC_P : 0)) * ES;
     const size_t out_bpp = direct ? 0 : (size_t)Cf::SC_P * ES;
     const size_t per_pair = in_bpp * o.stages + out_bpp;
-    const size_t cap = 200 * 1024;
+    const size_t fixed = (size_t)((shA ? shared_slot_elems<S>(Cf::SA_P) : 0) +
+                                  (shB ? shared_slot_elems<S>(Cf::SB_P) : 0)) * ES;
+    const size_t cap = 200 * 1024 - fixed;
     auto round_up = [&](int p) { return (p + quantum - 1) / quantum * quantum; };
     // R whole compute rounds, rounded down to the quantum (a few idle threads
     // in the last round) rather than up (a nearly empty extra round)
@@ -193,7 +255,9 @@ inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool 
         const int down = want / quantum * quantum;
         return down >= quantum ? down : round_up(want);
     };
-    int R = (int)(o.tile_bytes / ((size_t)Cf::MPR * in_bpp));
+    // (with both A and B shared and beta == 0 nothing is staged per pair)
+    const size_t in_eff = in_bpp ? in_bpp : (size_t)Cf::SC_P * ES;
+    int R = (int)(o.tile_bytes / ((size_t)Cf::MPR * in_eff));
     if (R < 1) R = 1;
     int P = rounds_to_P(R);
     while (P > quantum && (size_t)P * per_pair > cap) {
@@ -202,7 +266,7 @@ inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool 
     }
     if (P < quantum) P = quantum;
     // fill the GPU: at least two tiles per resident block when possible
-    int per_sm = (int)((227 * 1024) / ((size_t)P * per_pair + 1024));
+    int per_sm = (int)((227 * 1024) / ((size_t)P * per_pair + fixed + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2048 / Cf::NT) per_sm = 2048 / Cf::NT;
     if (o.ctas_per_sm > 0 && per_sm > o.ctas_per_sm) per_sm = o.ctas_per_sm;
@@ -212,7 +276,7 @@ inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool 
         int pn = round_up((int)(p2 < 1 ? 1 : p2));
         if (pn < P) P = pn;
     }
-    return Geom{P, (size_t)P * per_pair};
+    return Geom{P, (size_t)P * per_pair + fixed};
 }
 
 template <class Cf>
@@ -224,12 +288,14 @@ sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
     // flat-stream test per operand: minimal leading dimensions and 16-byte alignment
     auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     int flat = 0;
-    if (r.lda == Cf::RA && r.lda2 == (long long)Cf::SA && aligned(r.A)) flat |= 1;
-    if (r.ldb == Cf::RB && r.ldb2 == (long long)Cf::SB && aligned(r.B)) flat |= 2;
-    if (r.ldc == Cf::M && r.ldc2 == (long long)Cf::SC && aligned(r.C)) flat |= 4;
+    if (!r.Cp) {
+        if (r.lda == Cf::RA && r.lda2 == (long long)Cf::SA && aligned(r.A)) flat |= 1;
+        if (r.ldb == Cf::RB && r.ldb2 == (long long)Cf::SB && aligned(r.B)) flat |= 2;
+        if (r.ldc == Cf::M && r.ldc2 == (long long)Cf::SC && aligned(r.C)) flat |= 4;
+    }
     a.flat = flat;
     const bool direct = Cf::VS > 0 && (flat & 4);
-    const Geom gm = tile_geom<Cf>(r.batch, o, has_cold, direct);
+    const Geom gm = tile_geom<Cf>(r.batch, o, has_cold, direct, a.shared);
     a.P = gm.P;
     a.stages = o.stages;
     auto kern = pipe_kernel<Cf>;
@@ -306,17 +372,17 @@ generic_kernel(Args<Ty> g, int m, int n, int k, int ta, int tb)
         if (!alpha_zero) {
             for (int e = tid; e < cnt * sa; e += blockDim.x) {
                 const int q = e / sa, r = e - q * sa;
-                sA[e] = g.A_[(p0 + q) * g.lda2 + r % ra + (long long)(r / ra) * g.lda];
+                sA[e] = mat_of(g.A_, g.Ap, g.lda2, p0 + q)[r % ra + (long long)(r / ra) * g.lda];
             }
             for (int e = tid; e < cnt * sb; e += blockDim.x) {
                 const int q = e / sb, r = e - q * sb;
-                sB[e] = g.B_[(p0 + q) * g.ldb2 + r % rb + (long long)(r / rb) * g.ldb];
+                sB[e] = mat_of(g.B_, g.Bp, g.ldb2, p0 + q)[r % rb + (long long)(r / rb) * g.ldb];
             }
         }
         if (!beta_zero) {
             for (int e = tid; e < cnt * sc; e += blockDim.x) {
                 const int q = e / sc, r = e - q * sc;
-                sC[e] = g.C_[(p0 + q) * g.ldc2 + r % m + (long long)(r / m) * g.ldc];
+                sC[e] = mat_of(g.C_, g.Cp, g.ldc2, p0 + q)[r % m + (long long)(r / m) * g.ldc];
             }
         }
         __syncthreads();
@@ -336,7 +402,7 @@ generic_kernel(Args<Ty> g, int m, int n, int k, int ta, int tb)
                 }
                 A v = alpha_zero ? zero_a<A>() : mul(alpha, acc);
                 if (!beta_zero) v = axpy(beta, to_a(sC[q * sc + i + m * j]), v);
-                g.C_[(p0 + q) * g.ldc2 + i + (long long)j * g.ldc] = to_s<Ty>(v);
+                mat_of(g.C_, g.Cp, g.ldc2, p0 + q)[i + (long long)j * g.ldc] = to_s<Ty>(v);
             }
         }
         __syncthreads();
@@ -380,7 +446,7 @@ __global__ void scale_kernel(Args<Ty> g, int m, int n)
         const long long p = e / (m * n);
         const int r = (int)(e - p * m * n);
         const int i = r % m, j = r / m;
-        typename Ty::S* c = g.C_ + p * g.ldc2 + i + (long long)j * g.ldc;
+        typename Ty::S* c = mat_of(g.C_, g.Cp, g.ldc2, p) + i + (long long)j * g.ldc;
         *c = to_s<Ty>(bz ? zero_a<A>() : mul(beta, to_a(*c)));
     }
 }
@@ -409,7 +475,7 @@ sbgemm_status launch_shape_op(const Req& r, const LaunchOpts& o) {
 template <class Ty, int M, int N, int K>
 sbgemm_status launch_shape(const Req& r) {
     if (r.variant >= kNumPipeVariants) return launch_generic<Ty>(r);
-    const LaunchOpts o = pipe_variant(r.variant);
+    const LaunchOpts o = pipe_variant(r.variant, Ty::code);
     if (!r.ta && !r.tb) return launch_shape_op<Ty, M, N, K, false, false>(r, o);
     if (r.ta && !r.tb)  return launch_shape_op<Ty, M, N, K, true, false>(r, o);
     if (!r.ta && r.tb)  return launch_shape_op<Ty, M, N, K, false, true>(r, o);

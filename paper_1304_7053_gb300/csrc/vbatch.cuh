@@ -33,7 +33,7 @@ struct VItem {
 constexpr int kVKinds = 17;
 constexpr int kVGeneric = 16;
 constexpr int kVThreads = 128;
-constexpr int kVStageBytes = 20 * 1024;
+constexpr int kVStageBytes = 48 * 1024;
 constexpr int kVMaxTile = 128;
 
 template <class Ty>
@@ -56,15 +56,13 @@ struct VArgs {
 template <class Ty, int s>
 struct VKindCfg {
     static constexpr TileEntry te = tile_for(Ty::code, s, s, s, 0, 0);
-    using Cf = Cfg<Ty, s, s, s, false, false, te.tm, te.tn, te.si != 0, te.sj != 0, kVThreads>;
-    static constexpr bool ok = te.nt == kVThreads && Cf::MPR >= 1;
+    using Cf = Cfg<Ty, s, s, s, false, false, te.tm, te.tn, te.si != 0, te.sj != 0, te.nt>;
+    static constexpr bool ok = te.nt == kVThreads;
 };
 
 // Region offsets inside a stage are multiples of the tile's slot count
 // rounded up to this quantum, so every region starts 16-byte aligned for the
 // vector loads of the specialised compute.
-__host__ __device__ constexpr int gcd_c(int a, int b) { return b ? gcd_c(b, a % b) : a; }
-__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
 template <class Cf>
 __host__ __device__ constexpr int slot_quantum() {
     return lcm_c(lcm_c(16 / gcd_c(Cf::SA_P * Cf::ES, 16), 16 / gcd_c(Cf::SB_P * Cf::ES, 16)),
@@ -91,31 +89,69 @@ __device__ __forceinline__ void vcopy_elem(S* dst, const S* src) {
     else *dst = *src;
 }
 
-// Stage a tile: A, B of every problem (and old C where beta != 0) into slots
-// of SA_P / SB_P / SC_P elements.
+// Copy one matrix of `n` elements (contiguous in global memory) into a
+// shared-memory slot: the lanes of a warp take consecutive elements.
+template <class S, int ES>
+__device__ __forceinline__ void vcopy_matrix(S* dst, const S* src, int n, int lane) {
+    for (int e = lane; e < n; e += 32) vcopy_elem<S, ES>(dst + e, src + e);
+}
+
+// Stage a tile of a specialised kind (square size, compile-time slot sizes):
+// each warp takes whole problems; when a matrix is shorter than a warp, the
+// warp's lanes split into groups of SE lanes, one problem per group.
+template <class S, int SE, int SP, int NT>
+__device__ __forceinline__ void vstage_fixed(S* st, int which, const VRec* rec, int cnt,
+                                             const S* g, bool need_all) {
+    constexpr int ES = sizeof(S);
+    constexpr int PPW = SE >= 32 ? 1 : 32 / SE;         // problems per warp pass
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    const int sub = PPW > 1 ? lane / SE : 0;
+    const int l2 = PPW > 1 ? lane - sub * SE : lane;
+    if (PPW > 1 && sub >= PPW) return;
+    for (int q0 = warp * PPW; q0 < cnt; q0 += NW * PPW) {
+        const int q = q0 + sub;
+        if (q >= cnt) break;
+        const VRec& r = rec[q];
+        if (!need_all && (r.flags & 16)) continue;      // old C not needed (beta_q = 0)
+        const long long off = which == 0 ? r.a : which == 1 ? r.b : r.c;
+        const S* src = g + off;
+        S* dst = st + q * SP;
+        if (PPW > 1) vcopy_elem<S, ES>(dst + l2, src + l2);
+        else vcopy_matrix<S, ES>(dst, src, SE, lane);
+    }
+}
+
+// Stage a generic tile (run-time sizes): one warp per problem.
 template <class S, int NT>
 __device__ __forceinline__ void vstage(S* st, const VRec* rec, int cnt, const S* gA, const S* gB,
                                        const S* gC, int SA, int SB, int SC, int SA_P, int SB_P,
                                        int SC_P, int P, bool skip_ab, bool all_beta_zero) {
     constexpr int ES = sizeof(S);
-    const int tid = threadIdx.x;
-    if (!skip_ab) {
-        for (int e = tid; e < cnt * SA; e += NT) {
-            const int q = e / SA, r = e - q * SA;
-            vcopy_elem<S, ES>(st + q * SA_P + r, gA + rec[q].a + r);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    S* sB = st + P * SA_P;
+    S* sC = st + P * (SA_P + SB_P);
+    for (int q = warp; q < cnt; q += NW) {
+        const VRec& r = rec[q];
+        if (!skip_ab) {
+            vcopy_matrix<S, ES>(st + q * SA_P, gA + r.a, SA, lane);
+            vcopy_matrix<S, ES>(sB + q * SB_P, gB + r.b, SB, lane);
         }
-        S* sB = st + P * SA_P;
-        for (int e = tid; e < cnt * SB; e += NT) {
-            const int q = e / SB, r = e - q * SB;
-            vcopy_elem<S, ES>(sB + q * SB_P + r, gB + rec[q].b + r);
-        }
+        if (!all_beta_zero && !(r.flags & 16)) vcopy_matrix<S, ES>(sC + q * SC_P, gC + r.c, SC, lane);
     }
-    if (!all_beta_zero) {
-        S* sC = st + P * (SA_P + SB_P);
-        for (int e = tid; e < cnt * SC; e += NT) {
-            const int q = e / SC, r = e - q * SC;
-            if (!(rec[q].flags & 16)) vcopy_elem<S, ES>(sC + q * SC_P + r, gC + rec[q].c + r);
-        }
+}
+
+// Write the C slots of a tile back to each problem's C (one warp per problem).
+template <class S, int NT>
+__device__ __forceinline__ void vstore(S* gC, const S* sC, const VRec* rec, int cnt, int SC,
+                                       int SC_P) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    for (int q = warp; q < cnt; q += NW) {
+        S* dst = gC + rec[q].c;
+        const S* src = sC + q * SC_P;
+        for (int e = lane; e < SC; e += 32) dst[e] = src[e];
     }
 }
 
@@ -171,7 +207,7 @@ __device__ __forceinline__ void vcompute_generic(const typename Ty::S* st, const
         }
         A v = skip_ab ? zero_a<A>() : mul(alpha, acc);
         if (!(beta_zero || (fl & 16))) v = axpy(beta, to_a(sC[q * sc + i + m * j]), v);
-        sOut[q * sc + i + m * j] = to_s<Ty>(v);
+        sOut[q * sc + i + m * j] = to_s<Ty>(v);     // sOut is this tile's C slots: in place
     }
 }
 
@@ -184,11 +220,16 @@ __device__ __forceinline__ void vstage_kind(int kind, typename Ty::S* st, const 
             using K = VKindCfg<Ty, s>;
             if constexpr (K::ok) {
                 using Cf = typename K::Cf;
+                using S = typename Ty::S;
                 constexpr int Q = slot_quantum<Cf>();
                 const int P = (cnt + Q - 1) / Q * Q;
-                vstage<typename Ty::S, kVThreads>(st, rec, cnt, g.A_, g.B_, g.C_, Cf::SA, Cf::SB,
-                                                  Cf::SC, Cf::SA_P, Cf::SB_P, Cf::SC_P, P,
-                                                  skip_ab, all_bz);
+                if (!skip_ab) {
+                    vstage_fixed<S, Cf::SA, Cf::SA_P, kVThreads>(st, 0, rec, cnt, g.A_, true);
+                    vstage_fixed<S, Cf::SB, Cf::SB_P, kVThreads>(st + P * Cf::SA_P, 1, rec, cnt, g.B_, true);
+                }
+                if (!all_bz)
+                    vstage_fixed<S, Cf::SC, Cf::SC_P, kVThreads>(st + P * (Cf::SA_P + Cf::SB_P), 2, rec,
+                                                                 cnt, g.C_, false);
             }
             return;
         }
@@ -197,8 +238,8 @@ __device__ __forceinline__ void vstage_kind(int kind, typename Ty::S* st, const 
 }
 
 template <class Ty, int s = 1>
-__device__ __forceinline__ void vcompute_store_kind(int kind, const typename Ty::S* st,
-                                                    const VRec* rec, int cnt, typename Ty::S* sOut,
+__device__ __forceinline__ void vcompute_store_kind(int kind, typename Ty::S* st,
+                                                    const VRec* rec, int cnt,
                                                     const VArgs<Ty>& g, typename Ty::A alpha,
                                                     typename Ty::A beta, bool all_bz,
                                                     bool alpha_one, bool skip_ab) {
@@ -209,17 +250,17 @@ __device__ __forceinline__ void vcompute_store_kind(int kind, const typename Ty:
                 using Cf = typename K::Cf;
                 constexpr int Q = slot_quantum<Cf>();
                 const int P = (cnt + Q - 1) / Q * Q;
-                vcompute_kind<Cf>(st, rec, cnt, P, sOut, alpha, beta, all_bz, alpha_one, skip_ab);
+                // every entry of C has one owning thread, which reads its old
+                // value and writes the result in the same slot: C in place
+                typename Ty::S* sC = st + P * (Cf::SA_P + Cf::SB_P);
+                vcompute_kind<Cf>(st, rec, cnt, P, sC, alpha, beta, all_bz, alpha_one, skip_ab);
                 __syncthreads();
-                for (int e = threadIdx.x; e < cnt * Cf::SC; e += kVThreads) {
-                    const int q = e / Cf::SC, r = e - q * Cf::SC;
-                    g.C_[rec[q].c + r] = sOut[q * Cf::SC_P + r];
-                }
+                vstore<typename Ty::S, kVThreads>(g.C_, sC, rec, cnt, Cf::SC, Cf::SC_P);
             }
             return;
         }
-        vcompute_store_kind<Ty, s + 1>(kind, st, rec, cnt, sOut, g, alpha, beta, all_bz,
-                                       alpha_one, skip_ab);
+        vcompute_store_kind<Ty, s + 1>(kind, st, rec, cnt, g, alpha, beta, all_bz, alpha_one,
+                                       skip_ab);
     }
 }
 
@@ -239,7 +280,6 @@ __global__ void __launch_bounds__(kVThreads) vbatch_kernel(VArgs<Ty> g)
 
     S* stage[2] = {reinterpret_cast<S*>(smem_raw), reinterpret_cast<S*>(smem_raw + kVStageBytes)};
     VRec* recbase = reinterpret_cast<VRec*>(smem_raw + 2 * kVStageBytes);
-    S* sOut = reinterpret_cast<S*>(smem_raw + 2 * kVStageBytes + 3 * kVMaxTile * sizeof(VRec));
 
     A alpha = g.alpha, beta = g.beta;
     bool all_bz = g.beta_zero != 0, az = g.alpha_zero != 0;
@@ -305,16 +345,13 @@ __global__ void __launch_bounds__(kVThreads) vbatch_kernel(VArgs<Ty> g)
         if (ci.kind == kVGeneric) {
             const int m = ci.shape & 255, n = (ci.shape >> 8) & 255, k = (ci.shape >> 16) & 255;
             const int ta = (ci.shape >> 24) & 1, tb = (ci.shape >> 25) & 1;
-            vcompute_generic<Ty>(stage[b], rc, ci.count, ci.count, sOut, m, n, k, ta, tb,
+            S* sC = stage[b] + ci.count * (m * k + k * n);      // C slots: results in place
+            vcompute_generic<Ty>(stage[b], rc, ci.count, ci.count, sC, m, n, k, ta, tb,
                                  alpha, beta, all_bz, skip_ab);
             __syncthreads();
-            const int sc = m * n;
-            for (int e = tid; e < ci.count * sc; e += kVThreads) {
-                const int q = e / sc, r = e - q * sc;
-                g.C_[rc[q].c + r] = sOut[e];
-            }
+            vstore<S, kVThreads>(g.C_, sC, rc, ci.count, m * n, m * n);
         } else {
-            vcompute_store_kind<Ty>(ci.kind, stage[b], rc, ci.count, sOut, g, alpha, beta,
+            vcompute_store_kind<Ty>(ci.kind, stage[b], rc, ci.count, g, alpha, beta,
                                     all_bz, alpha_one, skip_ab);
         }
         if (nxt >= n_items) break;
@@ -329,7 +366,7 @@ __global__ void __launch_bounds__(kVThreads) vbatch_kernel(VArgs<Ty> g)
 }
 
 constexpr size_t vbatch_smem_bytes() {
-    return 3 * (size_t)kVStageBytes + 3 * (size_t)kVMaxTile * sizeof(VRec);
+    return 2 * (size_t)kVStageBytes + 3 * (size_t)kVMaxTile * sizeof(VRec);
 }
 
 // Host: kind table of one type, and the launcher.

@@ -79,9 +79,7 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
     if (count > 0 && !problems) return SBGEMM_ERR_NULL_POINTER;
     const size_t es = elem_bytes(type);
 
-    // bucket by (m, n, k, ta, tb); problems with m == 0 or n == 0 do nothing
-    using Key = std::tuple<int, int, int, int, int>;
-    std::map<Key, std::vector<int>> buckets;
+    // validate every problem first (nothing is allocated on error)
     for (int q = 0; q < count; ++q) {
         const sbgemm_vproblem& p = problems[q];
         if (p.m < 0 || p.n < 0 || p.k < 0 || p.m > 16 || p.n > 16 || p.k > 16)
@@ -89,55 +87,74 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
         const int opa = p.flags & 3, opb = (p.flags >> 2) & 3;
         if (opa == 3 || opb == 3) return SBGEMM_ERR_INVALID_TRANS;
         if (p.a < 0 || p.b < 0 || p.c < 0) return SBGEMM_ERR_INVALID_VALUE;
-        if (p.m == 0 || p.n == 0) continue;
-        buckets[Key(p.m, p.n, p.k, opa != 0, opb != 0)].push_back(q);
     }
 
+    // Bucket by (m, n, k, ta, tb) within windows of consecutive problems and
+    // queue the tiles window by window: problems that are neighbours in the
+    // arenas (and may share memory sectors) are then processed close in
+    // time, while their data is still in L2.  Problems with m == 0 or n == 0
+    // do nothing.
+    using Key = std::tuple<int, int, int, int, int>;
+    constexpr int kWindow = 4096;
     struct Tile { VItem it; double cost; };
     std::vector<Tile> tiles;
     std::vector<VRec> recs;
     recs.reserve(count);
-    for (auto& kv : buckets) {
-        int m, n, k, ta, tb;
-        std::tie(m, n, k, ta, tb) = kv.first;
-        const std::vector<int>& ids = kv.second;
-        int kind = kVGeneric;
-        if (m == n && n == k && !ta && !tb && kinfo[m - 1].mpr > 0) kind = m - 1;
-        int T;
-        if (kind != kVGeneric) {
-            const VKindInfo& ki = kinfo[kind];
-            // largest tile whose quantum-rounded slots fit one stage
-            T = kVMaxTile;
-            while (T > 1 && (size_t)((T + ki.quantum - 1) / ki.quantum * ki.quantum) * ki.bytes_per_pair
-                                > (size_t)kVStageBytes)
-                --T;
-            if (T >= ki.mpr) T = T / ki.mpr * ki.mpr;   // whole compute rounds
-        } else {
-            const size_t per = es * (size_t)(m * k + k * n + m * n);
-            T = (int)std::min<size_t>(kVMaxTile, per ? kVStageBytes / per : kVMaxTile);
-            if (T < 1) T = 1;
-        }
-        const int base = (int)recs.size();
-        for (int q : ids) {
+    std::map<Key, int> all_keys;
+    for (int w0 = 0; w0 < count; w0 += kWindow) {
+        const int w1 = std::min(count, w0 + kWindow);
+        std::map<Key, std::vector<int>> buckets;
+        for (int q = w0; q < w1; ++q) {
             const sbgemm_vproblem& p = problems[q];
-            VRec r;
-            r.a = p.a; r.b = p.b; r.c = p.c; r.flags = p.flags & 31; r.pad = 0;
-            recs.push_back(r);
+            if (p.m == 0 || p.n == 0) continue;
+            const int opa = p.flags & 3, opb = (p.flags >> 2) & 3;
+            buckets[Key(p.m, p.n, p.k, opa != 0, opb != 0)].push_back(q);
         }
-        const double unit = (double)es * (m * k + k * n + 2.0 * m * n) + 64.0;
-        for (int f = 0; f < (int)ids.size(); f += T) {
-            Tile t;
-            t.it.kind = kind;
-            t.it.first = base + f;
-            t.it.count = std::min(T, (int)ids.size() - f);
-            t.it.shape = m | (n << 8) | (k << 16) | (ta << 24) | (tb << 25);
-            t.cost = unit * t.it.count;
-            tiles.push_back(t);
+        std::vector<Tile> wtiles;
+        for (auto& kv : buckets) {
+            all_keys[kv.first] = 1;
+            int m, n, k, ta, tb;
+            std::tie(m, n, k, ta, tb) = kv.first;
+            const std::vector<int>& ids = kv.second;
+            int kind = kVGeneric;
+            if (m == n && n == k && !ta && !tb && kinfo[m - 1].mpr > 0) kind = m - 1;
+            int T;
+            if (kind != kVGeneric) {
+                const VKindInfo& ki = kinfo[kind];
+                // largest tile whose quantum-rounded slots fit one stage
+                T = kVMaxTile;
+                while (T > 1 && (size_t)((T + ki.quantum - 1) / ki.quantum * ki.quantum) * ki.bytes_per_pair
+                                    > (size_t)kVStageBytes)
+                    --T;
+                if (T >= ki.mpr) T = T / ki.mpr * ki.mpr;   // whole compute rounds
+            } else {
+                const size_t per = es * (size_t)(m * k + k * n + m * n);
+                T = (int)std::min<size_t>(kVMaxTile, per ? kVStageBytes / per : kVMaxTile);
+                if (T < 1) T = 1;
+            }
+            const int base = (int)recs.size();
+            for (int q : ids) {
+                const sbgemm_vproblem& p = problems[q];
+                VRec r;
+                r.a = p.a; r.b = p.b; r.c = p.c; r.flags = p.flags & 31; r.pad = 0;
+                recs.push_back(r);
+            }
+            const double unit = (double)es * (m * k + k * n + 2.0 * m * n) + 64.0;
+            for (int f = 0; f < (int)ids.size(); f += T) {
+                Tile t;
+                t.it.kind = kind;
+                t.it.first = base + f;
+                t.it.count = std::min(T, (int)ids.size() - f);
+                t.it.shape = m | (n << 8) | (k << 16) | (ta << 24) | (tb << 25);
+                t.cost = unit * t.it.count;
+                wtiles.push_back(t);
+            }
         }
+        // within a window, the most expensive tiles first
+        std::stable_sort(wtiles.begin(), wtiles.end(),
+                         [](const Tile& x, const Tile& y) { return x.cost > y.cost; });
+        tiles.insert(tiles.end(), wtiles.begin(), wtiles.end());
     }
-    // most expensive tiles first, so the queue's tail is short work
-    std::stable_sort(tiles.begin(), tiles.end(),
-                     [](const Tile& x, const Tile& y) { return x.cost > y.cost; });
 
     sbgemm_vplan pl = new (std::nothrow) sbgemm_vplan_s;
     if (!pl) return SBGEMM_ERR_CAPACITY;
@@ -145,7 +162,7 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
     pl->type = type;
     cudaGetDevice(&pl->device);
     pl->n_items = (int)tiles.size();
-    pl->n_buckets = (int)buckets.size();
+    pl->n_buckets = (int)all_keys.size();
     const size_t items_b = sizeof(VItem) * std::max<size_t>(1, tiles.size());
     const size_t recs_b = sizeof(VRec) * std::max<size_t>(1, recs.size());
     const size_t off_recs = (items_b + 255) / 256 * 256;

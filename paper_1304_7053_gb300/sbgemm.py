@@ -40,6 +40,14 @@ SIGNATURES = {
     "sbgemm_Bgemm_multi_uniform_async": (_i, _UNIFORM + [_i, _vp]),
     "sbgemm_gemm_multi_uniform_host": (_i, [_i] + _UNIFORM + [_vp, ctypes.c_size_t, _vp]),
     "sbgemm_gemm_grouped_host": (_i, [_i, _vp, _vp, _vp, _i, _vp, ctypes.c_size_t, _vp]),
+    "sbgemm_gemm_grouped": (_i, [_i, _vp, _vp, _vp, _i, _i, _vp]),
+    "sbgemm_grouped_config": (_i, [_i, _i, _i, _i]),
+    "sbgemm_Sgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),
+    "sbgemm_Dgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),
+    "sbgemm_Cgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),
+    "sbgemm_Zgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),
+    "sbgemm_gemm_multi_nounif": (_i, [_i, _c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i,
+                                      _i, _i, _vp]),
     "sbgemm_num_variants": (_i, [_i, _i, _i, _i]),
     "sbgemm_variant_name": (ctypes.c_char_p, [_i, _i, _i, _i, _i]),
     "sbgemm_gemm_multi_uniform_variant": (_i, [_i] + _UNIFORM + [_i, _i, _vp]),
@@ -174,6 +182,27 @@ def gemm_multi_uniform(dtype: str, transa: str, transb: str, m: int, n: int, k: 
     return st
 
 
+def gemm_multi_nounif(dtype: str, transa: str, transb: str, m: int, n: int, k: int,
+                      alpha, Aarray, lda: int, Barray, ldb: int, beta, Carray, ldc: int,
+                      batch: int, stream=None, device_scalars: bool = False,
+                      check: bool = True) -> int:
+    """Eq. (1) in the pointer-array form: Aarray, Barray, Carray are device
+    arrays (torch int64 CUDA tensors or raw addresses) of per-pair matrix
+    pointers.  Scalars as for ``gemm_multi_uniform``."""
+    if device_scalars:
+        pa, pb, mode, keep = _ptr(alpha), _ptr(beta), SCALARS_DEVICE, None
+    else:
+        ab, bb = _scalar_buf(dtype, alpha), _scalar_buf(dtype, beta)
+        pa, pb, mode, keep = ctypes.addressof(ab), ctypes.addressof(bb), SCALARS_HOST, (ab, bb)
+    st = lib().sbgemm_gemm_multi_nounif(TYPE_CODES[dtype], transa.encode(), transb.encode(), m, n,
+                                        k, pa, _ptr(Aarray), lda, _ptr(Barray), ldb, pb,
+                                        _ptr(Carray), ldc, batch, mode, _stream_ptr(stream))
+    del keep
+    if check and st != 0:
+        raise SbgemmError(st, "gemm_multi_nounif")
+    return st
+
+
 def prepare_uniform(dtype: str, transa: str, transb: str, m: int, n: int, k: int,
                     alpha, A, lda: int, lda2: int, B, ldb: int, ldb2: int,
                     beta, C, ldc: int, ldc2: int, batch: int, stream=None,
@@ -255,6 +284,24 @@ class HostGroup(ctypes.Structure):
                 ("hB", ctypes.c_void_p), ("ldb", ctypes.c_int), ("ldb2", ctypes.c_longlong),
                 ("hC", ctypes.c_void_p), ("ldc", ctypes.c_int), ("ldc2", ctypes.c_longlong),
                 ("batchCount", ctypes.c_int)]
+
+
+class Group(ctypes.Structure):
+    """``sbgemm_group``: one uniform batch on device arrays."""
+    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char),
+                ("m", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int), ("lda2", ctypes.c_longlong),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int), ("ldb2", ctypes.c_longlong),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int), ("ldc2", ctypes.c_longlong),
+                ("batchCount", ctypes.c_int)]
+
+
+def grouped_config(dtype: str, threads: int = 0, stage_bytes: int = 0, stages: int = 0) -> None:
+    """Launch configuration of the grouped persistent launch for one storage
+    type (all zero: the default)."""
+    st = lib().sbgemm_grouped_config(TYPE_CODES[dtype], threads, stage_bytes, stages)
+    if st != 0:
+        raise SbgemmError(st, "grouped_config")
 
 
 class VPlan:

@@ -12,8 +12,10 @@ cuBLAS strided-batched GEMM through torch.bmm on the same column-major data
 Sections: the fixed-size sweep (S/D/C/Z, m = 1..16, N = 1e3/1e5/1e6,
 op N/N, alpha = 1.5, beta in {0, -0.5}), the op sweep (complex single, all 9
 op pairs at N = 1e5), FEM-like rectangular shapes (S/D, N = 5e5, op(A) = T,
-beta = 1), and 16-bit storage (binary16/bfloat16, m in {8, 12, 16},
-N = 1e6).
+beta = 1), the interface comparison (3-D layout vs pointer arrays vs cuBLAS,
+N = 1e5), one A shared by all pairs (lda2 = 0, N = 1e6; algorithmic bytes
+count B and C only), and 16-bit storage (binary16/bfloat16, m in
+{8, 12, 16}, N = 1e6).
 """
 from __future__ import annotations
 
@@ -55,10 +57,14 @@ class Pools:
         return buf.view(t)
 
 
-def time_ours(pools, dtype, ta, tb, m, n, k, N, alpha, beta, reps, variant=None):
+def time_ours(pools, dtype, ta, tb, m, n, k, N, alpha, beta, reps, variant=None,
+              shared_a=False):
+    """Median time of the uniform call; ``shared_a``: lda2 = 0 (one A for
+    every pair)."""
     opa, opb = ta, tb
     ar, ac = (m, k) if opa == "N" else (k, m)
     br, bc = (k, n) if opb == "N" else (n, k)
+    lda2 = 0 if shared_a else ar * ac
     L = sbgemm.lib()
     ab, bb = sbgemm._scalar_buf(dtype, alpha), sbgemm._scalar_buf(dtype, beta)
     if variant is None:
@@ -67,13 +73,43 @@ def time_ours(pools, dtype, ta, tb, m, n, k, N, alpha, beta, reps, variant=None)
     ms = ctypes.c_float()
     s = pools.torch.cuda.current_stream().cuda_stream
     st = L.sbgemm_time_variant(sbgemm.TYPE_CODES[dtype], opa.encode(), opb.encode(), m, n, k,
-                               ctypes.addressof(ab), pools.A.data_ptr(), max(1, ar), ar * ac,
+                               ctypes.addressof(ab), pools.A.data_ptr(), max(1, ar), lda2,
                                pools.B.data_ptr(), max(1, br), br * bc, ctypes.addressof(bb),
                                pools.C.data_ptr(), max(1, m), m * n, N, variant, reps,
                                pools.flush.data_ptr(), pools.flush.numel(), s, ctypes.byref(ms))
     if st != 0:
         raise sbgemm.SbgemmError(st, "time_variant")
     return float(ms.value)
+
+
+def time_fn(pools, fn, reps):
+    """Median CUDA-event time of fn() on the current stream, L2 flushed
+    before every call."""
+    torch = pools.torch
+    ts = []
+    for _ in range(reps + 1):
+        pools.flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts = sorted(ts[1:])
+    return ts[len(ts) // 2]
+
+
+def time_nounif(pools, dtype, m, N, reps):
+    """The pointer-array form on the same flat data (pointer p -> matrix p),
+    op N/N, beta = 0; the pointer arrays are built outside the timing."""
+    torch = pools.torch
+    es = ES[dtype]
+    S = m * m
+    idx = torch.arange(N, device=pools.A.device, dtype=torch.int64) * (S * es)
+    Ap, Bp, Cp = idx + pools.A.data_ptr(), idx + pools.B.data_ptr(), idx + pools.C.data_ptr()
+    fn = lambda: sbgemm.gemm_multi_nounif(dtype, "N", "N", m, m, m, 1.0, Ap, m, Bp, m, 0.0, Cp,
+                                          m, N)
+    return time_fn(pools, fn, reps)
 
 
 def time_cublas(pools, dtype, m, n, k, N, reps):
@@ -121,7 +157,10 @@ def main(argv=None):
     ap.add_argument("--out", default="sweep.json")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
+    ap.add_argument("--sections", default="fixed,ops,fem,interface,shared_a,16bit",
+                    help="comma-separated subset of the sections to run")
     args = ap.parse_args(argv)
+    want = set(args.sections.split(","))
     import torch
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
@@ -136,32 +175,61 @@ def main(argv=None):
         print(json.dumps(r), flush=True)
 
     # fixed-size sweep, op N/N
-    for dtype in ("s", "d", "c", "z"):
-        for N in Ns:
-            for m in sizes:
-                for beta in (0.0, -0.5):
-                    alpha = 1.5
-                    ms = time_ours(pools, dtype, "N", "N", m, m, m, N, alpha, beta, args.reps)
-                    cb = time_cublas(pools, dtype, m, m, m, N, args.reps) if beta == 0.0 else None
-                    emit(row(dtype, "N", "N", m, m, m, N, beta, ms, cb), "fixed")
+    if "fixed" in want:
+        for dtype in ("s", "d", "c", "z"):
+            for N in Ns:
+                for m in sizes:
+                    for beta in (0.0, -0.5):
+                        alpha = 1.5
+                        ms = time_ours(pools, dtype, "N", "N", m, m, m, N, alpha, beta, args.reps)
+                        cb = time_cublas(pools, dtype, m, m, m, N, args.reps) if beta == 0.0 else None
+                        emit(row(dtype, "N", "N", m, m, m, N, beta, ms, cb), "fixed")
     # op sweep: complex single, N = 1e5, general alpha/beta
-    for m in sizes:
-        for ta in "NTC":
-            for tb in "NTC":
-                ms = time_ours(pools, "c", ta, tb, m, m, m, 100_000, 1.5 - 0.5j, -0.5 + 0.25j, args.reps)
-                emit(row("c", ta, tb, m, m, m, 100_000, -0.5, ms), "ops")
+    if "ops" in want:
+        for m in sizes:
+            for ta in "NTC":
+                for tb in "NTC":
+                    ms = time_ours(pools, "c", ta, tb, m, m, m, 100_000, 1.5 - 0.5j, -0.5 + 0.25j, args.reps)
+                    emit(row("c", ta, tb, m, m, m, 100_000, -0.5, ms), "ops")
     # FEM-like rectangular shapes
-    for dtype in ("s", "d"):
-        for (m, n, k) in ((4, 16, 4), (9, 16, 9), (16, 8, 16), (3, 9, 3), (16, 16, 1)):
-            ms = time_ours(pools, dtype, "T", "N", m, n, k, 500_000, 1.0, 1.0, args.reps)
-            emit(row(dtype, "T", "N", m, n, k, 500_000, 1.0, ms), "fem")
+    if "fem" in want:
+        for dtype in ("s", "d"):
+            for (m, n, k) in ((4, 16, 4), (9, 16, 9), (16, 8, 16), (3, 9, 3), (16, 16, 1)):
+                ms = time_ours(pools, dtype, "T", "N", m, n, k, 500_000, 1.0, 1.0, args.reps)
+                emit(row(dtype, "T", "N", m, n, k, 500_000, 1.0, ms), "fem")
+    # interface comparison (Section 7's cuBLAS comparison): the 3-D layout,
+    # the pointer-array form and cuBLAS strided batched, N = 1e5, beta = 0
+    if "interface" in want:
+        for dtype in ("s", "d", "c", "z"):
+            for m in sizes:
+                ms_u = time_ours(pools, dtype, "N", "N", m, m, m, 100_000, 1.0, 0.0, args.reps)
+                ms_p = time_nounif(pools, dtype, m, 100_000, args.reps)
+                cb = time_cublas(pools, dtype, m, m, m, 100_000, args.reps)
+                r = row(dtype, "N", "N", m, m, m, 100_000, 0.0, ms_u, cb)
+                r["nounif_ms"] = round(ms_p, 5)
+                r["nounif_gflops"] = round((8 if dtype in CPLX else 2) * m ** 3 * 100_000 / (ms_p * 1e-3) / 1e9, 1)
+                r["uniform_over_nounif"] = round(ms_p / ms_u, 2)
+                emit(r, "interface")
+    # one A shared by every pair (lda2 = 0) against a streamed A, N = 1e6
+    if "shared_a" in want:
+        for dtype in ("s", "d"):
+            for m in sizes:
+                ms_s = time_ours(pools, dtype, "N", "N", m, m, m, 1_000_000, 1.0, 0.0, args.reps,
+                                 shared_a=True)
+                ms_u = time_ours(pools, dtype, "N", "N", m, m, m, 1_000_000, 1.0, 0.0, args.reps)
+                r = row(dtype, "N", "N", m, m, m, 1_000_000, 0.0, ms_s)
+                r["gbps"] = round(ES[dtype] * 1_000_000 * 2 * m * m / (ms_s * 1e-3) / 1e9, 1)
+                r["streamed_a_ms"] = round(ms_u, 5)
+                r["speedup_vs_streamed_a"] = round(ms_u / ms_s, 2)
+                emit(r, "shared_a")
     # 16-bit storage
-    for dtype in ("h", "b"):
-        for m in (8, 12, 16):
-            for beta in (0.0, -0.5):
-                ms = time_ours(pools, dtype, "N", "N", m, m, m, 1_000_000, 1.5, beta, args.reps)
-                cb = time_cublas(pools, dtype, m, m, m, 1_000_000, args.reps) if beta == 0.0 else None
-                emit(row(dtype, "N", "N", m, m, m, 1_000_000, beta, ms, cb), "16bit")
+    if "16bit" in want:
+        for dtype in ("h", "b"):
+            for m in (8, 12, 16):
+                for beta in (0.0, -0.5):
+                    ms = time_ours(pools, dtype, "N", "N", m, m, m, 1_000_000, 1.5, beta, args.reps)
+                    cb = time_cublas(pools, dtype, m, m, m, 1_000_000, args.reps) if beta == 0.0 else None
+                    emit(row(dtype, "N", "N", m, m, m, 1_000_000, beta, ms, cb), "16bit")
     with open(args.out, "w") as f:
         json.dump(rows, f)
     return rows

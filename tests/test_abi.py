@@ -60,6 +60,33 @@ def test_argument_errors(kw, status):
     assert call(**kw) == status
 
 
+def call_nounif(dtype="s", ta="N", tb="N", m=2, n=2, k=2, lda=2, ldb=2, ldc=2, batch=1,
+                Ap=16, Bp=16, Cp=16, mode=0, alpha=True, beta=True):
+    a = sbgemm._scalar_buf(dtype, 1.0)
+    b = sbgemm._scalar_buf(dtype, 0.0)
+    return sbgemm.lib().sbgemm_gemm_multi_nounif(
+        sbgemm.TYPE_CODES[dtype], ta.encode(), tb.encode(), m, n, k,
+        ctypes.addressof(a) if alpha else None, Ap, lda, Bp, ldb,
+        ctypes.addressof(b) if beta else None, Cp, ldc, batch, mode, None)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(ta="X"), -1), (dict(m=17), -2), (dict(batch=-1), -2),
+    (dict(lda=1), -3), (dict(ldc=1), -3), (dict(tb="T", n=3, ldb=2, ldc=2), -3),
+    (dict(Cp=0), -4), (dict(beta=False), -4), (dict(Bp=0), -4),
+    (dict(mode=3), -5), (dict(dtype="b", n=0), 0), (dict(batch=0), 0), (dict(dtype=None), -5),
+])
+def test_nounif_argument_errors(kw, status):
+    """Pointer-array form: rejected before anything touches the device."""
+    if kw.get("dtype", "s") is None:
+        L = sbgemm.lib()
+        a = sbgemm._scalar_buf("s", 1.0)
+        assert L.sbgemm_gemm_multi_nounif(9, b"N", b"N", 2, 2, 2, ctypes.addressof(a), 16, 2, 16,
+                                          2, ctypes.addressof(a), 16, 2, 1, 0, None) == status
+        return
+    assert call_nounif(**kw) == status
+
+
 def test_status_strings_and_version():
     assert sbgemm.status_string(0) == "success"
     assert "trans" in sbgemm.status_string(-1)
@@ -95,3 +122,14 @@ def test_vbatch_plan_rejects_bad_problems():
     with pytest.raises(sbgemm.SbgemmError) as e:
         sbgemm.VPlan("s", p)
     assert e.value.status == -1
+
+
+def test_grouped_config_validation():
+    """Host-only: the grouped launch configuration accepts the documented
+    range and rejects the rest without changing the setting."""
+    L = sbgemm.lib()
+    assert L.sbgemm_grouped_config(0, 256, 16384, 4) == 0
+    assert L.sbgemm_grouped_config(0, 0, 0, 0) == 0
+    for bad in [(0, 64, 16384, 3), (0, 128, 2048, 3), (0, 128, 16384, 5), (0, 128, 16500, 3),
+                (0, 128, 65536, 4), (9, 128, 16384, 3), (0, 128, 16384, 1)]:
+        assert L.sbgemm_grouped_config(*bad) == -5, bad   # SBGEMM_ERR_INVALID_VALUE

@@ -1,0 +1,97 @@
+"""GPU parity of the grouped call: square N/N flat groups share one
+persistent launch, the other groups fall back to separate calls; every
+group's result is compared with the oracle."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1304_7053_gb300 import inputs, sbgemm
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def build(dtype, specs, int_valued):
+    groups = (sbgemm.Group * len(specs))()
+    keep = []
+    for g, (ta, tb, m, n, k, N, pad) in zip(groups, specs):
+        b = inputs.UniformBatch(dtype, ta, tb, m, n, k, N, seed=7 * m + n, int_valued=int_valued,
+                                pad_ld=pad, pad_ld2=pad)
+        tA, pA = H.to_dev(b.A)
+        tB, pB = H.to_dev(b.B)
+        tC, pC = H.to_dev(b.C)
+        g.transa, g.transb, g.m, g.n, g.k = ta.encode(), tb.encode(), m, n, k
+        g.A, g.lda, g.lda2 = pA, b.lda, b.lda2
+        g.B, g.ldb, g.ldb2 = pB, b.ldb, b.ldb2
+        g.C, g.ldc, g.ldc2 = pC, b.ldc, b.ldc2
+        g.batchCount = N
+        keep.append((b, tA, tB, tC))
+    return groups, keep
+
+
+@pytest.mark.parametrize("dtype", ["s", "d", "c", "z", "h"])
+@pytest.mark.parametrize("beta", [0.0, -0.5])
+def test_grouped_matches_oracle(dtype, beta):
+    int_valued = dtype in "sdcz"
+    specs = [("N", "N", s, s, s, 997 + 31 * s, 0) for s in range(1, 17)]
+    specs += [("T", "N", 5, 5, 5, 300, 0), ("N", "N", 4, 4, 4, 200, 1), ("N", "N", 3, 7, 2, 150, 0),
+              ("N", "N", 8, 8, 8, 0, 0)]
+    groups, keep = build(dtype, specs, int_valued)
+    alpha = 1.5
+    ab, bb = sbgemm._scalar_buf(dtype, alpha), sbgemm._scalar_buf(dtype, beta)
+    s = torch.cuda.current_stream()
+    st = sbgemm.lib().sbgemm_gemm_grouped(sbgemm.TYPE_CODES[dtype], ctypes.addressof(ab),
+                                          ctypes.addressof(bb), ctypes.addressof(groups), len(specs),
+                                          0, s.cuda_stream)
+    assert st == 0, sbgemm.status_string(st)
+    s.synchronize()
+    for b, tA, tB, tC in keep:
+        got, _ = H.from_dev(tC, b.C)
+        H.assert_parity(b, got, H.oracle_ref(b, alpha, beta), alpha, beta,
+                        exact=int_valued)
+
+
+def test_grouped_device_scalars_and_errors():
+    specs = [("N", "N", s, s, s, 500, 0) for s in (2, 9, 16)]
+    groups, keep = build("s", specs, False)
+    a = torch.tensor([1.5], device="cuda")
+    bta = torch.tensor([-0.5], device="cuda")
+    s = torch.cuda.current_stream()
+    st = sbgemm.lib().sbgemm_gemm_grouped(0, a.data_ptr(), bta.data_ptr(), ctypes.addressof(groups),
+                                          len(specs), 1, s.cuda_stream)
+    assert st == 0
+    s.synchronize()
+    for b, tA, tB, tC in keep:
+        H.assert_parity(b, H.from_dev(tC, b.C)[0], H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
+    # a bad group is rejected before anything runs
+    groups[1].lda = 1
+    ab = sbgemm._scalar_buf("s", 1.0)
+    st = sbgemm.lib().sbgemm_gemm_grouped(0, ctypes.addressof(ab), ctypes.addressof(ab),
+                                          ctypes.addressof(groups), len(specs), 0, s.cuda_stream)
+    assert st == -3
+
+
+@pytest.mark.parametrize("cfg", [(256, 16384, 4), (128, 8192, 2), (256, 65536, 2)])
+def test_grouped_launch_configurations(cfg):
+    """Every launch configuration gives the oracle's result (bit-exact on
+    small integers)."""
+    specs = [("N", "N", s, s, s, 700 + 13 * s, 0) for s in (1, 3, 4, 7, 8, 12, 13, 16)]
+    groups, keep = build("s", specs, True)
+    sbgemm.grouped_config("s", *cfg)
+    try:
+        ab, bb = sbgemm._scalar_buf("s", 1.5), sbgemm._scalar_buf("s", -0.5)
+        s = torch.cuda.current_stream()
+        st = sbgemm.lib().sbgemm_gemm_grouped(0, ctypes.addressof(ab), ctypes.addressof(bb),
+                                              ctypes.addressof(groups), len(specs), 0,
+                                              s.cuda_stream)
+        assert st == 0, sbgemm.status_string(st)
+        s.synchronize()
+    finally:
+        sbgemm.grouped_config("s")
+    for b, tA, tB, tC in keep:
+        H.assert_parity(b, H.from_dev(tC, b.C)[0], H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5,
+                        exact=True)

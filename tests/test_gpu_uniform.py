@@ -136,6 +136,28 @@ def test_shared_a_matrix_ld2_zero():
 
 
 @pytest.mark.parametrize("dtype", ["s", "d", "c", "z", "h", "b"])
+@pytest.mark.parametrize("shared", ["A", "B", "AB"])
+@pytest.mark.parametrize("shape", [("N", "N", 16, 16, 16), ("T", "C", 5, 7, 3),
+                                   ("N", "T", 8, 8, 8), ("N", "N", 1, 1, 1)])
+def test_shared_matrix_staged_once(dtype, shared, shape):
+    """ld2 = 0 for A and/or B: one matrix for every pair, staged once per
+    block; many tiles and a ragged last tile, beta zero and nonzero."""
+    ta, tb, m, n, k = shape
+    N = 2999
+    exact = dtype in "sdcz"
+    b = inputs.UniformBatch(dtype, ta, tb, m, n, k, N, seed=31 + m, int_valued=exact)
+    if "A" in shared:
+        b.A = b.A[:b.lda2].copy()
+        b.lda2 = 0
+    if "B" in shared:
+        b.B = b.B[:b.ldb2].copy()
+        b.ldb2 = 0
+    for beta in (0.0, -0.5):
+        got = H.run_gpu(b, 1.5, beta)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, beta), 1.5, beta, exact=exact)
+
+
+@pytest.mark.parametrize("dtype", ["s", "d", "c", "z", "h", "b"])
 def test_beta_zero_never_reads_c(dtype):
     """beta = 0: C filled with NaN must not reach the result."""
     m = 9
