@@ -217,7 +217,7 @@ sbgemm_status sbgemm_gemm_grouped(int type, const void* alpha, const void* beta,
  * bytes of one pipeline stage (4096..65536, a multiple of 1024) and pipeline
  * depth (2..4); the block's shared memory is stages*stage_bytes +
  * stage_bytes/2 and must stay within 220 KB.  All three zero restores the
- * default (128, 24576, 2).  Process-wide; not synchronised with calls
+ * default (128, 24576, 2; 128, 32768, 2 for D and Z).  Process-wide; not synchronised with calls
  * running concurrently on other host threads.  Invalid values give
  * SBGEMM_ERR_INVALID_VALUE and leave the configuration unchanged.
  */
@@ -331,6 +331,17 @@ typedef struct sbgemm_vplan_s* sbgemm_vplan;
 sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
                                         const sbgemm_vproblem* problems, int count);
 sbgemm_status sbgemm_vbatch_plan_destroy(sbgemm_vplan plan);
+
+/*
+ * Bucketing window of the plans created after this call: problems are
+ * bucketed within windows of `window` consecutive problems and the tiles
+ * are queued window by window (neighbours in the arenas, which may share
+ * memory sectors, are then processed close in time, at the price of blocks
+ * switching between size-specialised code more often).  0 restores the
+ * default, one window for the whole batch.  Process-wide; negative values
+ * give SBGEMM_ERR_INVALID_VALUE.
+ */
+sbgemm_status sbgemm_vbatch_config(int window);
 
 /*
  * Run a plan: one persistent kernel launch whose blocks take tiles from a

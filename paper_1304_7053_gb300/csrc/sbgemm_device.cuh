@@ -320,12 +320,12 @@ __device__ __forceinline__ P ldg_ptr(const P* a) {
     return reinterpret_cast<P>(__ldg(reinterpret_cast<const unsigned long long*>(a)));
 }
 
-// Pointer-array staging: matrix p0+q at ptrs[p0+q] with leading dimension
-// ld.  A matrix stored contiguously (ld == ROWS) whose start is 16-byte
-// aligned moves in 16-byte chunks; anything else moves element by element.
+// Pointer-array staging: matrix q of the tile at sptr[q] (the tile's
+// pointers, already in shared memory) with leading dimension ld.  A matrix
+// stored contiguously (ld == ROWS) whose start is 16-byte aligned moves in
+// 16-byte chunks; anything else moves element by element.
 template <class S, int SE, int SP, int ROWS, int NT>
-__device__ __forceinline__ void stage_ptrs(S* sdst, const S* const* ptrs, int ld, long long p0,
-                                           int cnt)
+__device__ __forceinline__ void stage_ptrs(S* sdst, const S* const* sptr, int ld, int cnt)
 {
     constexpr int ES = sizeof(S);
     const int tid = threadIdx.x;
@@ -335,7 +335,7 @@ __device__ __forceinline__ void stage_ptrs(S* sdst, const S* const* ptrs, int ld
             constexpr int EPC = 16 / ES;
             for (int c = tid; c < cnt * CPM; c += NT) {
                 const int q = c / CPM, r = c - q * CPM;
-                const S* src = ldg_ptr(ptrs + p0 + q) + r * EPC;
+                const S* src = sptr[q] + r * EPC;
                 S* dst = sdst + q * SP + r * EPC;
                 if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
                     cp_async16(dst, src, 16);
@@ -353,17 +353,16 @@ __device__ __forceinline__ void stage_ptrs(S* sdst, const S* const* ptrs, int ld
     for (int e = tid; e < cnt * SE; e += NT) {
         const int q = e / SE, r = e - q * SE;
         const int row = r % ROWS, col = r / ROWS;
-        const S* src = ldg_ptr(ptrs + p0 + q) + row + (long long)col * ld;
+        const S* src = sptr[q] + row + (long long)col * ld;
         S* dst = sdst + q * SP + r;
         if constexpr (ES == 4 || ES == 8 || ES == 16) cp_async_elem<ES>(dst, src);
         else *dst = *src;
     }
 }
 
-// Write cnt result matrices (slot stride SP) through a pointer array.
+// Write cnt result matrices (slot stride SP) to the matrices at sptr[q].
 template <class S, int SE, int SP, int ROWS, int NT>
-__device__ __forceinline__ void store_ptrs(S* const* ptrs, const S* ssrc, int ld, long long p0,
-                                           int cnt)
+__device__ __forceinline__ void store_ptrs(S* const* sptr, const S* ssrc, int ld, int cnt)
 {
     constexpr int ES = sizeof(S);
     const int tid = threadIdx.x;
@@ -373,7 +372,7 @@ __device__ __forceinline__ void store_ptrs(S* const* ptrs, const S* ssrc, int ld
             constexpr int EPC = 16 / ES;
             for (int c = tid; c < cnt * CPM; c += NT) {
                 const int q = c / CPM, r = c - q * CPM;
-                S* dst = ldg_ptr(ptrs + p0 + q) + r * EPC;
+                S* dst = sptr[q] + r * EPC;
                 const S* src = ssrc + q * SP + r * EPC;
                 if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
                     *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
@@ -388,7 +387,7 @@ __device__ __forceinline__ void store_ptrs(S* const* ptrs, const S* ssrc, int ld
     for (int e = tid; e < cnt * SE; e += NT) {
         const int q = e / SE, r = e - q * SE;
         const int row = r % ROWS, col = r / ROWS;
-        ldg_ptr(ptrs + p0 + q)[row + (long long)col * ld] = ssrc[q * SP + r];
+        sptr[q][row + (long long)col * ld] = ssrc[q * SP + r];
     }
 }
 

@@ -106,7 +106,9 @@ __host__ __device__ constexpr int shared_slot_elems(int slot_elems) {
 
 // ------------------------------------------------------------ pipelined kernel
 
-template <class Cf>
+// PF: the pointer-array form (a separate instantiation, so the 3-D layout
+// kernels carry none of its code or registers).
+template <class Cf, bool PF>
 __global__ void __launch_bounds__(Cf::NT)
 pipe_kernel(Args<typename Cf::Ty> g)
 {
@@ -146,19 +148,48 @@ pipe_kernel(Args<typename Cf::Ty> g)
     S* sOut = stage_base + stages * stage_elems;    // unused when C is stored directly
     S* sShA = sOut + (direct ? 0 : P * Cf::SC_P);
     S* sShB = sShA + (shA ? shared_slot_elems<S>(Cf::SA_P) : 0);
+    // Pointer-array form: a ring of 2*stages + 1 slots, each with one tile's
+    // A, B and C pointers.  The pointers of this block's tile j are fetched
+    // (cp.async) with the group of iteration j - 2*stages + 1, so they have
+    // arrived when the data of tile j is issued (iteration j - stages + 1),
+    // and they stay until tile j's C has been written (end of iteration j).
+    const S** sPtr = reinterpret_cast<const S**>(sShB + (shB ? shared_slot_elems<S>(Cf::SB_P) : 0));
+    constexpr bool ptr_form = PF;
+    const int ring = 2 * stages + 1;
+    auto ptr_slot = [&](int j) { return sPtr + (j % ring) * 3 * P; };
+    auto fetch_ptrs = [&](int j, bool async) {
+        const long long t = blockIdx.x + (long long)j * gridDim.x;
+        if (t >= ntiles) return;
+        const long long p0 = t * P;
+        const int cnt = (int)min((long long)P, batch - p0);
+        const S** d = ptr_slot(j);
+        for (int i = threadIdx.x; i < cnt; i += Cf::NT) {
+            if (async) {
+                cp_async_elem<8>(d + i, g.Ap + p0 + i);
+                cp_async_elem<8>(d + P + i, g.Bp + p0 + i);
+                cp_async_elem<8>(d + 2 * P + i, g.Cp + p0 + i);
+            } else {
+                d[i] = ldg_ptr(g.Ap + p0 + i);
+                d[P + i] = ldg_ptr(g.Bp + p0 + i);
+                d[2 * P + i] = ldg_ptr(g.Cp + p0 + i);
+            }
+        }
+    };
 
-    const bool ptr_form = g.Cp != nullptr;
     auto issue = [&](int t, int s) {
         S* st = stage_base + s * stage_elems;
         const long long p0 = (long long)t * P;
         const int cnt = (int)min((long long)P, batch - p0);
-        if (ptr_form) {
+        if constexpr (ptr_form) {
+            const S** pa = ptr_slot((t - (int)blockIdx.x) / (int)gridDim.x);
+            const S** pb = pa + P;
+            const S** pc = pb + P;
             if (!skip_ab) {
-                stage_ptrs<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.Ap, g.lda, p0, cnt);
-                stage_ptrs<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + offB, g.Bp, g.ldb, p0, cnt);
+                stage_ptrs<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, pa, g.lda, cnt);
+                stage_ptrs<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + offB, pb, g.ldb, cnt);
             }
             if (!beta_zero)
-                stage_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, g.Cp, g.ldc, p0, cnt);
+                stage_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, pc, g.ldc, cnt);
             return;
         }
         if (!skip_ab) {
@@ -177,9 +208,14 @@ pipe_kernel(Args<typename Cf::Ty> g)
         if (shB) stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(sShB, g.B_, 0, g.ldb, 0, 1, false);
     }
 
+    if constexpr (ptr_form) {
+        for (int j = 0; j < stages; ++j) fetch_ptrs(j, false);
+        __syncthreads();
+    }
     for (int s = 0; s < stages - 1; ++s) {
         const int t = blockIdx.x + s * gridDim.x;
         if (t < ntiles) issue(t, s);
+        if constexpr (ptr_form) fetch_ptrs(s + stages, true);
         cp_async_commit();
     }
 
@@ -193,6 +229,7 @@ pipe_kernel(Args<typename Cf::Ty> g)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int tn = t + (stages - 1) * gridDim.x;
         if (tn < ntiles) issue(tn, (it + stages - 1) % stages);
+        if constexpr (ptr_form) fetch_ptrs(it + 2 * stages - 1, true);
         cp_async_commit();
         cp_async_wait_dyn(stages - 1);
         __syncthreads();
@@ -210,8 +247,9 @@ pipe_kernel(Args<typename Cf::Ty> g)
         }
         // every thread is done reading this stage before it is refilled
         __syncthreads();
-        if (ptr_form)
-            store_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.Cp, sOut, g.ldc, p0, cnt);
+        if constexpr (ptr_form)
+            store_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(
+                const_cast<S* const*>(ptr_slot(it) + 2 * P), sOut, g.ldc, cnt);
         else if (!direct)
             store_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.C_, sOut, g.ldc2, g.ldc, p0, cnt, fc);
     }
@@ -232,7 +270,7 @@ struct Geom { int P; size_t smem; };
 
 template <class Cf>
 inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool direct,
-                      int shared = 0) {
+                      int shared = 0, bool ptr_form = false) {
     using S = typename Cf::S;
     constexpr int ES = Cf::ES;
     const bool shA = shared & 1, shB = shared & 2;
@@ -243,7 +281,10 @@ inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool 
     const size_t in_bpp =
         (size_t)((shA ? 0 : Cf::SA_P) + (shB ? 0 : Cf::SB_P) + (has_cold ? Cf::SC_P : 0)) * ES;
     const size_t out_bpp = direct ? 0 : (size_t)Cf::SC_P * ES;
-    const size_t per_pair = in_bpp * o.stages + out_bpp;
+    // the pointer-array form keeps three pointers per pair in each of
+    // 2*stages + 1 ring slots
+    const size_t per_pair = in_bpp * o.stages + out_bpp +
+                            (ptr_form ? 3 * sizeof(void*) * (2 * o.stages + 1) : 0);
     const size_t fixed = (size_t)((shA ? shared_slot_elems<S>(Cf::SA_P) : 0) +
                                   (shB ? shared_slot_elems<S>(Cf::SB_P) : 0)) * ES;
     const size_t cap = 200 * 1024 - fixed;
@@ -279,8 +320,8 @@ inline Geom tile_geom(long long batch, const LaunchOpts& o, bool has_cold, bool 
     return Geom{P, (size_t)P * per_pair + fixed};
 }
 
-template <class Cf>
-sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
+template <class Cf, bool PF>
+sbgemm_status launch_pipe_k(const Req& r, const LaunchOpts& o) {
     using Ty = typename Cf::Ty;
     Args<Ty> a;
     fill_args(a, r);
@@ -295,10 +336,10 @@ sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
     }
     a.flat = flat;
     const bool direct = Cf::VS > 0 && (flat & 4);
-    const Geom gm = tile_geom<Cf>(r.batch, o, has_cold, direct, a.shared);
+    const Geom gm = tile_geom<Cf>(r.batch, o, has_cold, direct, a.shared, PF);
     a.P = gm.P;
     a.stages = o.stages;
-    auto kern = pipe_kernel<Cf>;
+    auto kern = pipe_kernel<Cf, PF>;
     static bool attr_set = false;   // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -339,6 +380,11 @@ sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
     cudaError_t le = cudaLaunchKernelEx(&lc, kern, a);
     if (le != cudaSuccess) return (sbgemm_status)le;
     return (sbgemm_status)cudaGetLastError();
+}
+
+template <class Cf>
+sbgemm_status launch_pipe(const Req& r, const LaunchOpts& o) {
+    return r.Cp ? launch_pipe_k<Cf, true>(r, o) : launch_pipe_k<Cf, false>(r, o);
 }
 
 // ------------------------------------------------------------ generic kernel

@@ -33,8 +33,24 @@ struct VItem {
 constexpr int kVKinds = 17;
 constexpr int kVGeneric = 16;
 constexpr int kVThreads = 128;
-constexpr int kVStageBytes = 48 * 1024;
 constexpr int kVMaxTile = 128;
+constexpr int kVBlocksPerSM = 2;
+// problems per bucketing window of a plan: by default the whole batch, so
+// each bucket's tiles are contiguous in the queue and all blocks run the
+// same size-specialised code at once (windows of 4096 problems made the
+// blocks switch kinds nearly every tile: 1.8x slower on the fp32 mix)
+constexpr int kVDefaultWindow = 1 << 30;
+
+// Pipeline shape per storage type.  Memory-bound types keep two tiles of
+// 24 KB in flight; fp64 and complex128, bound by the fp64 pipe, take 48 KB
+// stages (more matrices per compute round) with one tile in flight.
+// Shared memory: stages x stage bytes + (2 stages - 1) record buffers of
+// kVMaxTile records, two blocks per SM either way.
+__host__ __device__ constexpr bool vfp64(int type) { return type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z; }
+__host__ __device__ constexpr int vstages_of(int type) { return vfp64(type) ? 2 : 3; }
+__host__ __device__ constexpr int vstage_bytes_of(int type) { return vfp64(type) ? 48 * 1024 : 24 * 1024; }
+__host__ __device__ constexpr int vrec_slots_of(int type) { return 2 * vstages_of(type) - 1; }
+__host__ __device__ constexpr int vitem_slots_of(int type) { return 3 * vstages_of(type) - 2; }
 
 template <class Ty>
 struct VArgs {
@@ -96,29 +112,48 @@ __device__ __forceinline__ void vcopy_matrix(S* dst, const S* src, int n, int la
     for (int e = lane; e < n; e += 32) vcopy_elem<S, ES>(dst + e, src + e);
 }
 
-// Stage a tile of a specialised kind (square size, compile-time slot sizes):
-// each warp takes whole problems; when a matrix is shorter than a warp, the
-// warp's lanes split into groups of SE lanes, one problem per group.
-template <class S, int SE, int SP, int NT>
-__device__ __forceinline__ void vstage_fixed(S* st, int which, const VRec* rec, int cnt,
-                                             const S* g, bool need_all) {
+// Copy one contiguous matrix of SE elements into its slot: in 16-byte
+// chunks when its byte size is a multiple of 16 and its start is 16-byte
+// aligned (lanes l0, l0+LPP, ... take the chunks), element by element
+// otherwise.
+template <class S, int SE, int LPP>
+__device__ __forceinline__ void vcopy_square(S* dst, const S* src, int l0) {
     constexpr int ES = sizeof(S);
-    constexpr int PPW = SE >= 32 ? 1 : 32 / SE;         // problems per warp pass
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr ((SE * ES) % 16 == 0) {
+        constexpr int CPM = SE * ES / 16, EPC = 16 / ES;
+        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+#pragma unroll
+            for (int c = l0; c < CPM; c += LPP) cp_async16(dst + c * EPC, src + c * EPC, 16);
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = l0; e < SE; e += LPP) vcopy_elem<S, ES>(dst + e, src + e);
+}
+
+// Stage the A, B (and old C) matrices of a tile of a square specialised
+// kind.  A group of LPP lanes takes one problem: it reads the problem's
+// record once and copies its three matrices; a warp takes 32 / LPP problems
+// per pass (LPP = the chunk or element count of one matrix, at most 32).
+template <class S, int SE, int SP, int NT>
+__device__ __forceinline__ void vstage_square(S* sA, S* sB, S* sC, const VRec* rec, int cnt,
+                                              const S* gA, const S* gB, const S* gC, bool ab,
+                                              bool any_c) {
+    constexpr int ES = sizeof(S);
+    constexpr int UNITS = (SE * ES) % 16 == 0 ? SE * ES / 16 : SE;   // chunks or elements
+    constexpr int LPP = UNITS >= 32 ? 32 : UNITS;
+    constexpr int PPW = 32 / LPP;
     constexpr int NW = NT / 32;
-    const int sub = PPW > 1 ? lane / SE : 0;
-    const int l2 = PPW > 1 ? lane - sub * SE : lane;
-    if (PPW > 1 && sub >= PPW) return;
-    for (int q0 = warp * PPW; q0 < cnt; q0 += NW * PPW) {
-        const int q = q0 + sub;
-        if (q >= cnt) break;
-        const VRec& r = rec[q];
-        if (!need_all && (r.flags & 16)) continue;      // old C not needed (beta_q = 0)
-        const long long off = which == 0 ? r.a : which == 1 ? r.b : r.c;
-        const S* src = g + off;
-        S* dst = st + q * SP;
-        if (PPW > 1) vcopy_elem<S, ES>(dst + l2, src + l2);
-        else vcopy_matrix<S, ES>(dst, src, SE, lane);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / LPP, l0 = lane - sub * LPP;
+    if (sub >= PPW) return;                             // lanes left over when LPP does not divide 32
+    for (int q = warp * PPW + sub; q < cnt; q += NW * PPW) {
+        const VRec r = rec[q];
+        if (ab) {
+            vcopy_square<S, SE, LPP>(sA + q * SP, gA + r.a, l0);
+            vcopy_square<S, SE, LPP>(sB + q * SP, gB + r.b, l0);
+        }
+        if (any_c && !(r.flags & 16)) vcopy_square<S, SE, LPP>(sC + q * SP, gC + r.c, l0);
     }
 }
 
@@ -139,6 +174,36 @@ __device__ __forceinline__ void vstage(S* st, const VRec* rec, int cnt, const S*
             vcopy_matrix<S, ES>(sB + q * SB_P, gB + r.b, SB, lane);
         }
         if (!all_beta_zero && !(r.flags & 16)) vcopy_matrix<S, ES>(sC + q * SC_P, gC + r.c, SC, lane);
+    }
+}
+
+// Write the C slots of a square specialised tile back to each problem's C,
+// with the lane mapping of vstage_square (16-byte stores where size and
+// alignment allow).
+template <class S, int SE, int SP, int NT>
+__device__ __forceinline__ void vstore_fixed(S* gC, const S* sC, const VRec* rec, int cnt) {
+    constexpr int ES = sizeof(S);
+    constexpr int UNITS = (SE * ES) % 16 == 0 ? SE * ES / 16 : SE;
+    constexpr int LPP = UNITS >= 32 ? 32 : UNITS;
+    constexpr int PPW = 32 / LPP;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / LPP, l0 = lane - sub * LPP;
+    if (sub >= PPW) return;
+    for (int q = warp * PPW + sub; q < cnt; q += NW * PPW) {
+        S* dst = gC + rec[q].c;
+        const S* src = sC + q * SP;
+        if constexpr ((SE * ES) % 16 == 0) {
+            constexpr int CPM = SE * ES / 16, EPC = 16 / ES;
+            if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                for (int c = l0; c < CPM; c += LPP)
+                    *reinterpret_cast<uint4*>(dst + c * EPC) = *reinterpret_cast<const uint4*>(src + c * EPC);
+                continue;
+            }
+        }
+#pragma unroll
+        for (int e = l0; e < SE; e += LPP) dst[e] = src[e];
     }
 }
 
@@ -223,13 +288,11 @@ __device__ __forceinline__ void vstage_kind(int kind, typename Ty::S* st, const 
                 using S = typename Ty::S;
                 constexpr int Q = slot_quantum<Cf>();
                 const int P = (cnt + Q - 1) / Q * Q;
-                if (!skip_ab) {
-                    vstage_fixed<S, Cf::SA, Cf::SA_P, kVThreads>(st, 0, rec, cnt, g.A_, true);
-                    vstage_fixed<S, Cf::SB, Cf::SB_P, kVThreads>(st + P * Cf::SA_P, 1, rec, cnt, g.B_, true);
-                }
-                if (!all_bz)
-                    vstage_fixed<S, Cf::SC, Cf::SC_P, kVThreads>(st + P * (Cf::SA_P + Cf::SB_P), 2, rec,
-                                                                 cnt, g.C_, false);
+                static_assert(Cf::SA == Cf::SB && Cf::SB == Cf::SC && Cf::SA_P == Cf::SC_P,
+                              "square kinds share one slot size");
+                vstage_square<S, Cf::SA, Cf::SA_P, kVThreads>(
+                    st, st + P * Cf::SA_P, st + P * (Cf::SA_P + Cf::SB_P), rec, cnt, g.A_, g.B_,
+                    g.C_, !skip_ab, !all_bz);
             }
             return;
         }
@@ -255,7 +318,7 @@ __device__ __forceinline__ void vcompute_store_kind(int kind, typename Ty::S* st
                 typename Ty::S* sC = st + P * (Cf::SA_P + Cf::SB_P);
                 vcompute_kind<Cf>(st, rec, cnt, P, sC, alpha, beta, all_bz, alpha_one, skip_ab);
                 __syncthreads();
-                vstore<typename Ty::S, kVThreads>(g.C_, sC, rec, cnt, Cf::SC, Cf::SC_P);
+                vstore_fixed<typename Ty::S, Cf::SC, Cf::SC_P, kVThreads>(g.C_, sC, rec, cnt);
             }
             return;
         }
@@ -265,21 +328,36 @@ __device__ __forceinline__ void vcompute_store_kind(int kind, typename Ty::S* st
 }
 
 template <class Ty>
-__global__ void __launch_bounds__(kVThreads) vbatch_kernel(VArgs<Ty> g)
+__global__ void __launch_bounds__(kVThreads, kVBlocksPerSM) vbatch_kernel(VArgs<Ty> g)
 {
-    // Pipeline per block, iteration i:
-    //   wait for group i-1 (data of tile i, records of tile i+1);
-    //   issue group i: data of tile i+1, records of tile i+2 (its index was
-    //   popped from the queue during iteration i-1);
-    //   pop the index of tile i+3 (its latency overlaps the compute);
-    //   compute tile i and write its C.
+    // Software pipeline of one block over the tiles it takes from the queue
+    // (its j-th tile is "tile j"; D = pipeline stages).  Every tile needs, in order:
+    // its queue index, its descriptor (VItem), its records, its data.  Each
+    // is fetched asynchronously D - 1 iterations before the next step needs
+    // it, all in the one cp.async group an iteration commits:
+    //   iteration j waits for group j - D + 1, then issues
+    //     data of tile j + D - 1      (records arrived with group j - D + 1)
+    //     records of tile j + 2D - 2  (descriptor arrived with group j - D + 1)
+    //     descriptor of tile j + 3D - 3 (index popped during iteration j - 1)
+    //   and computes tile j while D - 1 tiles of data are in flight.
+    // Queue indices of one block increase, so the first empty descriptor
+    // (an index past the end) ends the block's work.
     using S = typename Ty::S;
     using A = typename Ty::A;
+    constexpr int D = vstages_of(Ty::code);
+    constexpr int kStageBytes = vstage_bytes_of(Ty::code);
+    constexpr int kRecSlots = vrec_slots_of(Ty::code);
+    constexpr int kItemSlots = vitem_slots_of(Ty::code);
+    constexpr int kLead = 3 * D - 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_item[4];
+    __shared__ int s_base;
 
-    S* stage[2] = {reinterpret_cast<S*>(smem_raw), reinterpret_cast<S*>(smem_raw + kVStageBytes)};
-    VRec* recbase = reinterpret_cast<VRec*>(smem_raw + 2 * kVStageBytes);
+    VRec* recbase = reinterpret_cast<VRec*>(smem_raw + D * kStageBytes);
+    VItem* sitem = reinterpret_cast<VItem*>(smem_raw + D * kStageBytes +
+                                            kRecSlots * kVMaxTile * sizeof(VRec));
+    auto stage_of = [&](int t) { return reinterpret_cast<S*>(smem_raw + (t % D) * kStageBytes); };
+    auto recs_of = [&](int t) { return recbase + (t % kRecSlots) * kVMaxTile; };
+    auto item_of = [&](int t) -> VItem& { return sitem[t % kItemSlots]; };
 
     A alpha = g.alpha, beta = g.beta;
     bool all_bz = g.beta_zero != 0, az = g.alpha_zero != 0;
@@ -290,18 +368,21 @@ __global__ void __launch_bounds__(kVThreads) vbatch_kernel(VArgs<Ty> g)
     const int tid = threadIdx.x;
     const int n_items = g.n_items;
 
-    // asynchronous copy of a tile's records into record buffer slot rb
-    auto issue_recs = [&](int item, int rb) {
-        if (item >= n_items) return;
-        const VItem it = g.items[item];
+    // records of tile t (its descriptor is in shared memory)
+    auto issue_recs = [&](int t) {
+        const VItem it = item_of(t);
+        if (it.count == 0) return;
         const char* src = reinterpret_cast<const char*>(g.recs + it.first);
-        char* dst = reinterpret_cast<char*>(recbase + rb * kVMaxTile);
+        char* dst = reinterpret_cast<char*>(recs_of(t));
         for (int c = tid; c < it.count * 2; c += kVThreads)     // 16-byte halves of 32-byte records
             cp_async16(dst + 16 * c, src + 16 * c, 16);
     };
-    auto issue_data = [&](int item, S* st, const VRec* rb) {
-        if (item >= n_items) return;
-        const VItem it = g.items[item];
+    // data of tile t (its records are in shared memory)
+    auto issue_data = [&](int t) {
+        const VItem it = item_of(t);
+        if (it.count == 0) return;
+        S* st = stage_of(t);
+        const VRec* rb = recs_of(t);
         if (it.kind == kVGeneric) {
             const int m = it.shape & 255, n = (it.shape >> 8) & 255, k = (it.shape >> 16) & 255;
             vstage<S, kVThreads>(st, rb, it.count, g.A_, g.B_, g.C_, m * k, k * n, m * n, m * k,
@@ -311,62 +392,73 @@ __global__ void __launch_bounds__(kVThreads) vbatch_kernel(VArgs<Ty> g)
         }
     };
 
-    // prologue: tiles 0, 1 and 2 of this block
-    if (tid < 3) s_item[tid] = atomicAdd(g.counter, 1);
+    // prologue: queue indices of tiles 0 .. kLead-1 in one pop, descriptors
+    // by plain loads, records of tiles 0 .. 2D-3, then data of tiles
+    // 0 .. D-2 (one group each)
+    if (tid == 0) s_base = atomicAdd(g.counter, kLead);
     __syncthreads();
-    int item0 = s_item[0], item1 = s_item[1], item2 = s_item[2];
-    if (item0 >= n_items) return;
-    issue_recs(item0, 0);
+    const int base = s_base;
+    if (base >= n_items) return;
+    int pend = n_items;
+    if (tid == 0) pend = atomicAdd(g.counter, 1);                 // tile kLead
+    for (int t = tid; t < kLead; t += kVThreads) {
+        VItem v = {0, 0, 0, 0};
+        if (base + t < n_items) v = g.items[base + t];
+        item_of(t) = v;
+    }
+    __syncthreads();
+    for (int t = 0; t < 2 * D - 2; ++t) issue_recs(t);
     cp_async_commit();
     cp_async_wait_dyn(0);
     __syncthreads();
-    issue_data(item0, stage[0], recbase);
-    issue_recs(item1, 1);
-    cp_async_commit();
-    int pend = 0;
-    if (tid == 0) pend = atomicAdd(g.counter, 1);   // tile 3
-
-    int cur = item0, nxt = item1, nxt2 = item2;
-    for (int it = 0;; ++it) {
-        const int b = it & 1;
-        const int rcur = it % 3, rnxt = (it + 1) % 3, rnxt2 = (it + 2) % 3;
-        cp_async_wait_dyn(0);          // data of cur, records of nxt
-        if (tid == 0) s_item[3] = pend;
-        __syncthreads();
-        const int nxt3 = s_item[3];
-        issue_data(nxt, stage[b ^ 1], recbase + rnxt * kVMaxTile);
-        issue_recs(nxt2, rnxt2);
+    for (int t = 0; t < D - 1; ++t) {
+        issue_data(t);
         cp_async_commit();
-        if (tid == 0 && nxt3 < n_items) pend = atomicAdd(g.counter, 1);
-        else if (tid == 0) pend = n_items;
+    }
 
-        const VItem ci = g.items[cur];
-        const VRec* rc = recbase + rcur * kVMaxTile;
+    for (int j = 0;; ++j) {
+        cp_async_wait_dyn(D - 2);      // data of tile j, records of j+D-1, descriptor of j+2D-2
+        __syncthreads();
+        const VItem ci = item_of(j);
+        if (ci.count == 0) break;
+        issue_data(j + D - 1);
+        issue_recs(j + 2 * D - 2);
+        if (tid == 0) {
+            VItem* dst = &item_of(j + kLead);
+            if (pend < n_items) {
+                cp_async16(dst, g.items + pend, 16);
+                pend = atomicAdd(g.counter, 1);    // tile j + kLead + 1; read next iteration
+            } else {
+                *dst = VItem{0, 0, 0, 0};
+            }
+        }
+        cp_async_commit();
+
+        const VRec* rc = recs_of(j);
+        S* st = stage_of(j);
         if (ci.kind == kVGeneric) {
             const int m = ci.shape & 255, n = (ci.shape >> 8) & 255, k = (ci.shape >> 16) & 255;
             const int ta = (ci.shape >> 24) & 1, tb = (ci.shape >> 25) & 1;
-            S* sC = stage[b] + ci.count * (m * k + k * n);      // C slots: results in place
-            vcompute_generic<Ty>(stage[b], rc, ci.count, ci.count, sC, m, n, k, ta, tb,
+            S* sC = st + ci.count * (m * k + k * n);      // C slots: results in place
+            vcompute_generic<Ty>(st, rc, ci.count, ci.count, sC, m, n, k, ta, tb,
                                  alpha, beta, all_bz, skip_ab);
             __syncthreads();
             vstore<S, kVThreads>(g.C_, sC, rc, ci.count, m * n, m * n);
         } else {
-            vcompute_store_kind<Ty>(ci.kind, stage[b], rc, ci.count, g, alpha, beta,
+            vcompute_store_kind<Ty>(ci.kind, st, rc, ci.count, g, alpha, beta,
                                     all_bz, alpha_one, skip_ab);
         }
-        if (nxt >= n_items) break;
-        // the copy-out above reads sOut and the record buffer of cur: every
-        // thread is past it before they are refilled
+        // every thread is past this tile's stage, records and descriptor
+        // before the next iteration refills them
         __syncthreads();
-        cur = nxt;
-        nxt = nxt2;
-        nxt2 = nxt3;
     }
     cp_async_wait_dyn(0);
 }
 
-constexpr size_t vbatch_smem_bytes() {
-    return 2 * (size_t)kVStageBytes + 3 * (size_t)kVMaxTile * sizeof(VRec);
+constexpr size_t vbatch_smem_bytes(int type) {
+    return (size_t)vstages_of(type) * vstage_bytes_of(type) +
+           (size_t)vrec_slots_of(type) * kVMaxTile * sizeof(VRec) +
+           (size_t)vitem_slots_of(type) * sizeof(VItem);
 }
 
 // Host: kind table of one type, and the launcher.
@@ -399,7 +491,7 @@ sbgemm_status vbatch_launch(const VItem* items, int n_items, const VRec* recs, i
         g.beta_zero = beta_zero; g.alpha_zero = alpha_zero;
     }
     g.max_tile = kVMaxTile;
-    const size_t smem = vbatch_smem_bytes();
+    const size_t smem = vbatch_smem_bytes(Ty::code);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(vbatch_kernel<Ty>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -38,6 +38,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 struct TileRule {
     int T[16];     // tile size of square N/N kind s+1, 0 when the kind is not specialised
     int es;        // storage element bytes
+    int stage;     // bytes of one pipeline stage of the type
 };
 
 __device__ __forceinline__ int key_of(const sbgemm_vproblem& p, bool* valid) {
@@ -65,7 +66,7 @@ __device__ __forceinline__ int tile_of(int key, const TileRule& rule, int* kind)
     }
     *kind = kVGeneric;
     const int per = rule.es * (m * k + k * n + m * n);
-    int T = per > 0 ? kVStageBytes / per : kVMaxTile;
+    int T = per > 0 ? rule.stage / per : kVMaxTile;
     if (T > kVMaxTile) T = kVMaxTile;
     return T < 1 ? 1 : T;
 }
@@ -230,12 +231,13 @@ extern "C" sbgemm_status sbgemm_vbatch_run_noalloc(int type, const sbgemm_vprobl
     // whose quantum-rounded slots fit one stage)
     TileRule rule;
     rule.es = es;
+    rule.stage = vstage_bytes_of(type);
     for (int s = 0; s < 16; ++s) {
         const VKindInfo& ki = kinfo[s];
         if (ki.mpr <= 0) { rule.T[s] = 0; continue; }
         int T = kVMaxTile;
         while (T > 1 && (size_t)((T + ki.quantum - 1) / ki.quantum * ki.quantum) * ki.bytes_per_pair
-                            > (size_t)kVStageBytes)
+                            > (size_t)rule.stage)
             --T;
         if (T >= ki.mpr) T = T / ki.mpr * ki.mpr;
         rule.T[s] = T;

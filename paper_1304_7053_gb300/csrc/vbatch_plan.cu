@@ -64,9 +64,19 @@ bool host_zero(int type, const void* p) {
 }
 
 }  // namespace
+
+// problems per bucketing window of a plan (sbgemm_vbatch_config)
+int g_window = kVDefaultWindow;
+
 }  // namespace sbg
 
 extern "C" {
+
+sbgemm_status sbgemm_vbatch_config(int window) {
+    if (window < 0) return SBGEMM_ERR_INVALID_VALUE;
+    sbg::g_window = window == 0 ? sbg::kVDefaultWindow : window;
+    return SBGEMM_SUCCESS;
+}
 
 sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
                                         const sbgemm_vproblem* problems, int count) {
@@ -95,7 +105,7 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
     // time, while their data is still in L2.  Problems with m == 0 or n == 0
     // do nothing.
     using Key = std::tuple<int, int, int, int, int>;
-    constexpr int kWindow = 4096;
+    const int kWindow = g_window;
     struct Tile { VItem it; double cost; };
     std::vector<Tile> tiles;
     std::vector<VRec> recs;
@@ -124,12 +134,12 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
                 // largest tile whose quantum-rounded slots fit one stage
                 T = kVMaxTile;
                 while (T > 1 && (size_t)((T + ki.quantum - 1) / ki.quantum * ki.quantum) * ki.bytes_per_pair
-                                    > (size_t)kVStageBytes)
+                                    > (size_t)vstage_bytes_of(type))
                     --T;
                 if (T >= ki.mpr) T = T / ki.mpr * ki.mpr;   // whole compute rounds
             } else {
                 const size_t per = es * (size_t)(m * k + k * n + m * n);
-                T = (int)std::min<size_t>(kVMaxTile, per ? kVStageBytes / per : kVMaxTile);
+                T = (int)std::min<size_t>(kVMaxTile, per ? vstage_bytes_of(type) / per : kVMaxTile);
                 if (T < 1) T = 1;
             }
             const int base = (int)recs.size();

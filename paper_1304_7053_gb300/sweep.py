@@ -15,7 +15,9 @@ op pairs at N = 1e5), FEM-like rectangular shapes (S/D, N = 5e5, op(A) = T,
 beta = 1), the interface comparison (3-D layout vs pointer arrays vs cuBLAS,
 N = 1e5), one A shared by all pairs (lda2 = 0, N = 1e6; algorithmic bytes
 count B and C only), and 16-bit storage (binary16/bfloat16, m in
-{8, 12, 16}, N = 1e6).
+{8, 12, 16}, N = 1e6).  ``grouped_config`` (only when named) sweeps the
+launch configuration of the grouped call on the fp32 and fp64 sizes 1..16
+workload.
 """
 from __future__ import annotations
 
@@ -112,6 +114,70 @@ def time_nounif(pools, dtype, m, N, reps):
     return time_fn(pools, fn, reps)
 
 
+def grouped_config_sweep(dtype, dev, reps=200, N=100_000):
+    """Wall time per ``sbgemm_gemm_grouped`` call over the square N/N batches
+    m = 1..16 (N pairs each, alpha = 1, beta = 0) for every launch
+    configuration (threads x stage bytes x depth) that fits; the batches
+    (1.8 GB fp32) are far above L2, so calls run back to back."""
+    import torch
+    tdt = {"s": torch.float32, "d": torch.float64}[dtype]
+    L = sbgemm.lib()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1)
+    sizes = list(range(1, 17))
+    bufs = {m: tuple(torch.rand(N * m * m, device=dev, generator=gen, dtype=tdt) for _ in range(3))
+            for m in sizes}
+    groups = (sbgemm.Group * len(sizes))()
+    for gr, m in zip(groups, sizes):
+        A, B, C = bufs[m]
+        gr.transa, gr.transb, gr.m, gr.n, gr.k = b"N", b"N", m, m, m
+        gr.A, gr.lda, gr.lda2 = A.data_ptr(), m, m * m
+        gr.B, gr.ldb, gr.ldb2 = B.data_ptr(), m, m * m
+        gr.C, gr.ldc, gr.ldc2 = C.data_ptr(), m, m * m
+        gr.batchCount = N
+    one, zero = _scalar_pair(dtype)
+    stream = torch.cuda.Stream(device=dev)
+    flops = sum(2 * m ** 3 * N for m in sizes)
+
+    def call():
+        st = L.sbgemm_gemm_grouped(sbgemm.TYPE_CODES[dtype], ctypes.addressof(one),
+                                   ctypes.addressof(zero), ctypes.addressof(groups), len(sizes),
+                                   0, stream.cuda_stream)
+        if st != 0:
+            raise sbgemm.SbgemmError(st, "gemm_grouped")
+
+    out = []
+    try:
+        for threads in (128, 256):
+            for sb in (8192, 12288, 16384, 24576, 32768, 49152):
+                for stg in (2, 3, 4):
+                    if stg * sb + sb // 2 > 220 * 1024:
+                        continue
+                    sbgemm.grouped_config(dtype, threads, sb, stg)
+                    with torch.cuda.stream(stream):
+                        for _ in range(5):
+                            call()
+                        t0 = torch.cuda.Event(enable_timing=True)
+                        t1 = torch.cuda.Event(enable_timing=True)
+                        t0.record(stream)
+                        for _ in range(reps):
+                            call()
+                        t1.record(stream)
+                    torch.cuda.synchronize()
+                    us = t0.elapsed_time(t1) / reps * 1e3
+                    out.append({"dtype": dtype, "threads": threads, "stage_bytes": sb, "stages": stg,
+                                "smem_bytes": stg * sb + sb // 2, "us_per_call": round(us, 1),
+                                "gflops": round(flops / (us * 1e-6) / 1e9, 1)})
+    finally:
+        sbgemm.grouped_config(dtype)
+    return out
+
+
+def _scalar_pair(dtype):
+    c = ctypes.c_float if dtype == "s" else ctypes.c_double
+    return (c * 1)(1.0), (c * 1)(0.0)
+
+
 def time_cublas(pools, dtype, m, n, k, N, reps):
     """cuBLAS strided batched (torch.bmm) on column-major N/N data, beta = 0."""
     torch = pools.torch
@@ -158,7 +224,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
     ap.add_argument("--sections", default="fixed,ops,fem,interface,shared_a,16bit",
-                    help="comma-separated subset of the sections to run")
+                    help="comma-separated subset of the sections to run "
+                         "(grouped_config runs only when named)")
     args = ap.parse_args(argv)
     want = set(args.sections.split(","))
     import torch
@@ -167,6 +234,17 @@ def main(argv=None):
     rows = []
     Ns = [100_000] if args.quick else [1_000, 100_000, 1_000_000]
     sizes = [2, 4, 8, 10, 12, 16] if args.quick else list(range(1, 17))
+    if "grouped_config" in want:
+        for dtype in ("s", "d"):
+            for r in grouped_config_sweep(dtype, dev):
+                r["section"] = "grouped_config"
+                rows.append(r)
+                print(json.dumps(r), flush=True)
+        want.discard("grouped_config")
+        if not want:
+            with open(args.out, "w") as f:
+                json.dump(rows, f)
+            return rows
     pools = Pools(16 * 256 * 1_000_000 + 4096, dev)
 
     def emit(r, section):

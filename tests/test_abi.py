@@ -133,3 +133,12 @@ def test_grouped_config_validation():
     for bad in [(0, 64, 16384, 3), (0, 128, 2048, 3), (0, 128, 16384, 5), (0, 128, 16500, 3),
                 (0, 128, 65536, 4), (9, 128, 16384, 3), (0, 128, 16384, 1)]:
         assert L.sbgemm_grouped_config(*bad) == -5, bad   # SBGEMM_ERR_INVALID_VALUE
+
+
+def test_vbatch_window_config_validation():
+    """Host-only: the plan's bucketing window accepts 0 (default) and any
+    positive count, and rejects negative values."""
+    L = sbgemm.lib()
+    assert L.sbgemm_vbatch_config(-1) == -5   # SBGEMM_ERR_INVALID_VALUE
+    assert L.sbgemm_vbatch_config(65536) == 0
+    assert L.sbgemm_vbatch_config(0) == 0
