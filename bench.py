@@ -66,6 +66,8 @@ def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1304_7053_gb300", "csrc")
     for fn in sorted(os.listdir(d)):
+        if not fn.endswith((".cu", ".cuh", ".h")):
+            continue
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())

@@ -217,7 +217,7 @@ sbgemm_status sbgemm_gemm_grouped(int type, const void* alpha, const void* beta,
  * bytes of one pipeline stage (4096..65536, a multiple of 1024) and pipeline
  * depth (2..4); the block's shared memory is stages*stage_bytes +
  * stage_bytes/2 and must stay within 220 KB.  All three zero restores the
- * default (128, 24576, 2; 128, 32768, 2 for D and Z).  Process-wide; not synchronised with calls
+ * default (128, 28672, 2).  Process-wide; not synchronised with calls
  * running concurrently on other host threads.  Invalid values give
  * SBGEMM_ERR_INVALID_VALUE and leave the configuration unchanged.
  */

@@ -21,10 +21,7 @@ SBG_GDECL(S) SBG_GDECL(D) SBG_GDECL(C) SBG_GDECL(Z) SBG_GDECL(H) SBG_GDECL(B)
 namespace {
 
 // launch configuration per storage type (sbgemm_grouped_config)
-// (fp64 and complex128 take 32 KB stages: a sweep on fp64 sizes 1..16 put
-// 32 KB x 2 first, 8-24 KB stages underfill the fp64 compute rounds)
-constexpr GConfig kGDefault64 = {128, 32 * 1024, 2};
-GConfig g_config[6] = {kGDefault, kGDefault64, kGDefault, kGDefault64, kGDefault, kGDefault};
+GConfig g_config[6] = {kGDefault, kGDefault, kGDefault, kGDefault, kGDefault, kGDefault};
 
 bool gkinds(int type, int threads, GKindInfo* k) {
     switch (type) {
@@ -136,7 +133,7 @@ extern "C" sbgemm_status sbgemm_grouped_config(int type, int threads, int stage_
     using namespace sbg;
     if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
     if (threads == 0 && stage_bytes == 0 && stages == 0) {
-        g_config[type] = (type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z) ? kGDefault64 : kGDefault;
+        g_config[type] = kGDefault;
         return SBGEMM_SUCCESS;
     }
     const GConfig c = {threads, stage_bytes, stages};

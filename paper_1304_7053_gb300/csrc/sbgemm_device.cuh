@@ -222,6 +222,11 @@ struct Cfg {
         : (TM % (16 / ES) == 0 && M % (16 / ES) == 0 && SC % (16 / ES) == 0) ? 16 / ES : 0;
     static_assert(MPR >= 1, "threads per matrix exceeds block size");
     static_assert(K % VL == 0, "l-chunk must divide k");
+    // l-chunks per unrolled body of the product loop: about 128 FMAs per
+    // body, so the large shapes keep a short loop instead of one fully
+    // unrolled body (smaller code, fewer instruction-cache misses when
+    // several shapes share one kernel)
+    static constexpr int UL = (TM * TN * VL >= 128) ? 1 : (128 / (TM * TN * VL));
 };
 
 // ------------------------------------------------------------ staging
@@ -483,7 +488,7 @@ __device__ __forceinline__ void compute_block(const typename Cf::S* __restrict__
         for (int c = 0; c < TN; ++c) acc[r][c] = zero_a<A>();
 
     if (!skip_ab) {
-#pragma unroll
+#pragma unroll Cf::UL
         for (int l0 = 0; l0 < K; l0 += VL) {
             A av[TM][VL], bv[TN][VL];
             if constexpr (Cf::TA) {

@@ -149,7 +149,7 @@ def grouped_config_sweep(dtype, dev, reps=200, N=100_000):
     out = []
     try:
         for threads in (128, 256):
-            for sb in (8192, 12288, 16384, 24576, 32768, 49152):
+            for sb in (8192, 16384, 20480, 24576, 28672, 32768, 40960, 49152):
                 for stg in (2, 3, 4):
                     if stg * sb + sb // 2 > 220 * 1024:
                         continue
