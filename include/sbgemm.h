@@ -468,6 +468,15 @@ sbgemm_status sbgemm_mlp_adam(long long n, float* params, const float* grads, fl
 /* ------------------------------------------------------------------ */
 
 /* Static description of a status code (never NULL). */
+/*
+ * Kernels that wait on hardware barriers (bulk copies) bound every wait; a
+ * wait that expires records SBGEMM_ERR_TIMEOUT in a per-device error word
+ * and the kernel stops early (its results are then incomplete).  This call
+ * waits for `stream`, returns the word in *code (0: no expired wait since
+ * the last call) and clears it.
+ */
+sbgemm_status sbgemm_device_error(int* code, void* stream);
+
 const char* sbgemm_status_string(sbgemm_status status);
 
 /* Library version as major*10000 + minor*100 + patch. */

@@ -30,6 +30,22 @@ int num_sms() {
     return cache[dev];
 }
 
+// Error word written by kernels whose bounded waits expire (one per
+// device, in this module; kernels of other modules get its address).
+__device__ int g_device_error;
+
+int* device_error_ptr() {
+    static int* cache[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!cache[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+        cache[dev] = static_cast<int*>(p);
+    }
+    return cache[dev];
+}
+
 namespace {
 
 int op_code(char t) {
@@ -345,6 +361,22 @@ const char* sbgemm_status_string(sbgemm_status s) {
     case SBGEMM_ERR_CAPACITY: return "request exceeds a fixed capacity";
     default: return s > 0 ? cudaGetErrorString((cudaError_t)s) : "unknown status";
     }
+}
+
+sbgemm_status sbgemm_device_error(int* code, void* stream) {
+    if (!code) return SBGEMM_ERR_NULL_POINTER;
+    *code = 0;
+    int* p = sbg::device_error_ptr();
+    if (!p) return SBGEMM_ERR_NOT_SUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(p, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return (sbgemm_status)e;
+    *code = v;
+    return SBGEMM_SUCCESS;
 }
 
 int sbgemm_version(void) { return 100; }

@@ -143,6 +143,116 @@ __device__ __forceinline__ void cp_async_wait_dyn(int pending) {
     else                   asm volatile("cp.async.wait_group 3;\n" ::: "memory");
 }
 
+// ------------------------------------------------------------ bulk copies (TMA, 1-D)
+
+// Spin limit of every mbarrier wait: each try_wait may itself suspend the
+// thread for a while, so this bounds a wait to well under a second of a
+// healthy copy's latency many times over; on expiry the kernel records
+// SBGEMM_ERR_TIMEOUT in the caller's error word and stops.
+constexpr long long kSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the asynchronous (copy) proxy
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// one arrival that also announces `bytes` of copies completing on the barrier
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// wait for the phase with the given parity to complete; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// global -> shared bulk copy completing on `bar` (16-byte aligned addresses,
+// size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(smem_u32(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// shared -> global bulk copy in the issuing thread's bulk group
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+                 :: "l"(gdst), "r"(smem_u32(ssrc)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// the issuing thread's bulk stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// the issuing thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// order this thread's shared-memory writes before later copy-proxy reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Stage `cnt` consecutive matrices of a flat operand (SE elements each,
+// matrix p0 at g + p0*SE, 16-byte aligned) into slots of SP elements with
+// bulk copies on `bar`: one copy of the whole span when the slots are
+// unpadded (a ragged end of under 16 bytes is copied by thread 0 with plain
+// loads), one copy per matrix when they are padded.  Returns the bytes that
+// complete on the barrier (the same on every thread).
+template <class S, int SE, int SP, int NT>
+__device__ __forceinline__ unsigned stage_bulk(S* sdst, const S* g, long long p0, int cnt, uint64_t* bar) {
+    constexpr int ES = sizeof(S);
+    const S* src = g + p0 * (long long)SE;
+    // (the callers' tile geometry makes both ends 16-byte aligned; should
+    // that ever fail, the tile is copied with plain loads instead)
+    if (((reinterpret_cast<uintptr_t>(src) | smem_u32(sdst)) & 15) != 0) {
+        for (int e = threadIdx.x; e < cnt * SE; e += NT) sdst[(e / SE) * SP + e % SE] = src[e];
+        return 0;
+    }
+    if constexpr (SP == SE) {
+        const unsigned nbytes = (unsigned)(cnt * SE * ES);
+        const unsigned body = nbytes & ~15u;
+        if (threadIdx.x == 0) {
+            if (body) bulk_g2s(sdst, src, body, bar);
+            for (unsigned e = body / ES; e < nbytes / ES; ++e) sdst[e] = src[e];
+        }
+        return body;
+    } else {
+        static_assert((SE * ES) % 16 == 0, "padded slots hold whole 16-byte chunks");
+        for (int q = threadIdx.x; q < cnt; q += NT) bulk_g2s(sdst + q * SP, src + q * SE, SE * ES, bar);
+        return (unsigned)(cnt * SE * ES);
+    }
+}
+
+// Write `cnt` result matrices from slots of SP elements to a flat C with
+// bulk stores (the issuing threads commit a bulk group each); a ragged end
+// of under 16 bytes is written by thread 0 directly.  The slots must have
+// been written before a fence_proxy_async and a block barrier.
+template <class S, int SE, int SP, int NT>
+__device__ __forceinline__ void store_bulk(S* g, const S* ssrc, long long p0, int cnt) {
+    constexpr int ES = sizeof(S);
+    S* dst = g + p0 * (long long)SE;
+    if (((reinterpret_cast<uintptr_t>(dst) | smem_u32(ssrc)) & 15) != 0) {
+        for (int e = threadIdx.x; e < cnt * SE; e += NT) dst[e] = ssrc[(e / SE) * SP + e % SE];
+        return;
+    }
+    if constexpr (SP == SE) {
+        const unsigned nbytes = (unsigned)(cnt * SE * ES);
+        const unsigned body = nbytes & ~15u;
+        if (threadIdx.x == 0) {
+            if (body) { bulk_s2g(dst, ssrc, body); bulk_commit(); }
+            for (unsigned e = body / ES; e < nbytes / ES; ++e) dst[e] = ssrc[e];
+        }
+    } else {
+        static_assert((SE * ES) % 16 == 0, "padded slots hold whole 16-byte chunks");
+        if ((int)threadIdx.x < cnt) {
+            for (int q = threadIdx.x; q < cnt; q += NT) bulk_s2g(dst + q * SE, ssrc + q * SP, SE * ES);
+            bulk_commit();
+        }
+    }
+}
+
 // ------------------------------------------------------------ launch args
 
 template <class Ty>
@@ -166,6 +276,7 @@ struct Args {
     int alpha_zero;              // host mode: alpha == 0 known on the host
     int P;                       // pairs per tile
     int stages;                  // pipeline depth (2..4)
+    int* err;                    // device error word (SBGEMM_ERR_TIMEOUT on an expired wait)
 };
 
 // Pad a matrix slot by one 16-byte chunk when its byte size is an even number
@@ -316,6 +427,29 @@ __device__ __forceinline__ void store_operand(S* g, const S* ssrc, long long ld2
             g[(p0 + q) * ld2 + row + (long long)col * ld] = ssrc[q * SP + r];
         }
     }
+}
+
+// Stage a flat operand tile: with BULK and unpadded slots, one bulk copy of
+// the whole span on `bar`; else 16-byte cp.async chunks (one bulk copy per
+// matrix into padded slots measured slower: many small copies of 0.25-1 KB
+// for fp32 m = 8, 12, 16).  Returns the bytes that complete on the barrier.
+template <class S, int SE, int SP, int ROWS, int NT, bool BULK>
+__device__ __forceinline__ unsigned stage_flat(S* sdst, const S* g, long long p0, int cnt, uint64_t* bar) {
+    if constexpr (BULK && SP == SE) {
+        return stage_bulk<S, SE, SP, NT>(sdst, g, p0, cnt, bar);
+    } else {
+        stage_operand<S, SE, SP, ROWS, NT>(sdst, g, SE, ROWS, p0, cnt, true);
+        return 0;
+    }
+}
+
+// Write a tile of results to a flat C: with BULK and unpadded slots one bulk
+// store of the span, else 16-byte stores.  The caller has fenced its
+// shared-memory writes (fence_proxy_async) and passed a block barrier.
+template <class S, int SE, int SP, int ROWS, int NT, bool BULK>
+__device__ __forceinline__ void store_flat(S* g, const S* ssrc, long long p0, int cnt) {
+    if constexpr (BULK && SP == SE) store_bulk<S, SE, SP, NT>(g, ssrc, p0, cnt);
+    else store_operand<S, SE, SP, ROWS, NT>(g, ssrc, SE, ROWS, p0, cnt, true);
 }
 
 // One pointer from a read-only device array, through the non-coherent

@@ -54,7 +54,8 @@ inline LaunchOpts pipe_variant(int v, int type_code = 0) {
     }
 }
 
-int num_sms();  // cached device attribute (api.cu)
+int num_sms();            // cached device attribute (api.cu)
+int* device_error_ptr();  // the current device's error word (api.cu)
 
 template <class Ty>
 inline void fill_args(Args<Ty>& a, const Req& r) {
@@ -84,6 +85,7 @@ inline void fill_args(Args<Ty>& a, const Req& r) {
     a.Cp = reinterpret_cast<S* const*>(r.Cp);
     a.shared = r.Cp ? 0 : (r.lda2 == 0 ? 1 : 0) | (r.ldb2 == 0 ? 2 : 0);
     a.flat = 0;
+    a.err = device_error_ptr();
 }
 
 // Base of matrix p of an operand: pointer-array form or 3-D layout.
@@ -176,6 +178,28 @@ pipe_kernel(Args<typename Cf::Ty> g)
         }
     };
 
+    // Flat operands with unpadded slots of at least 480 bytes per matrix move
+    // by one bulk copy per tile (measured faster for fp32 m = 11..15, slower
+    // for smaller matrices, whose tiles are better served by many parallel
+    // 16-byte cp.async requests).  Shapes with such an operand keep one
+    // barrier per stage: the k-th use of stage s completes phase k once its
+    // bulk copies have landed.
+    constexpr int kBulkMin = 480;
+    constexpr bool bulkA = !PF && Cf::SA_P == Cf::SA && Cf::SA * Cf::ES >= kBulkMin;
+    constexpr bool bulkB = !PF && Cf::SB_P == Cf::SB && Cf::SB * Cf::ES >= kBulkMin;
+    constexpr bool bulkC = !PF && Cf::SC_P == Cf::SC && Cf::SC * Cf::ES >= kBulkMin;
+    constexpr bool kBulk = bulkA || bulkB || bulkC;
+    __shared__ uint64_t s_bar[4];
+    __shared__ int s_fail;
+    if constexpr (kBulk) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < stages; ++s) mbar_init(&s_bar[s], 1);
+            mbar_fence_init();
+            s_fail = 0;
+        }
+        __syncthreads();
+    }
+
     auto issue = [&](int t, int s) {
         S* st = stage_base + s * stage_elems;
         const long long p0 = (long long)t * P;
@@ -192,14 +216,28 @@ pipe_kernel(Args<typename Cf::Ty> g)
                 stage_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, pc, g.ldc, cnt);
             return;
         }
+        // flat operands move by bulk copies on the stage's barrier where
+        // they pay (stage_flat); strided ones element by element (cp.async)
+        uint64_t* bar = &s_bar[s];
+        unsigned bytes = 0;
         if (!skip_ab) {
-            if (!shA)
-                stage_operand<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.A_, g.lda2, g.lda, p0, cnt, fa);
-            if (!shB)
-                stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + offB, g.B_, g.ldb2, g.ldb, p0, cnt, fb);
+            if (!shA) {
+                if (fa) bytes += stage_flat<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT, bulkA>(st, g.A_, p0, cnt, bar);
+                else stage_operand<S, Cf::SA, Cf::SA_P, Cf::RA, Cf::NT>(st, g.A_, g.lda2, g.lda, p0, cnt, false);
+            }
+            if (!shB) {
+                if (fb) bytes += stage_flat<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT, bulkB>(st + offB, g.B_, p0, cnt, bar);
+                else stage_operand<S, Cf::SB, Cf::SB_P, Cf::RB, Cf::NT>(st + offB, g.B_, g.ldb2, g.ldb, p0, cnt,
+                                                                        false);
+            }
         }
-        if (!beta_zero)
-            stage_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, g.C_, g.ldc2, g.ldc, p0, cnt, fc);
+        if (!beta_zero) {
+            if (fc) bytes += stage_flat<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT, bulkC>(st + offC, g.C_, p0, cnt, bar);
+            else stage_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(st + offC, g.C_, g.ldc2, g.ldc, p0, cnt, false);
+        }
+        if constexpr (kBulk) {
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes);
+        }
     };
 
     // the shared matrices join the first commit group
@@ -226,13 +264,32 @@ pipe_kernel(Args<typename Cf::Ty> g)
     const bool active = ql < Cf::MPR;
 
     int it = 0;
+    bool failed = false;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int tn = t + (stages - 1) * gridDim.x;
         if (tn < ntiles) issue(tn, (it + stages - 1) % stages);
         if constexpr (ptr_form) fetch_ptrs(it + 2 * stages - 1, true);
         cp_async_commit();
         cp_async_wait_dyn(stages - 1);
-        __syncthreads();
+        if constexpr (kBulk) {
+            // thread 0 waits for the stage's bulk copies (the block barrier
+            // then orders its observation before every thread's reads) and
+            // for its previous bulk stores to have read the output tile
+            if (threadIdx.x == 0) {
+                if (!mbar_wait(&s_bar[it % stages], (it / stages) & 1)) {
+                    s_fail = 1;
+                    if (g.err) atomicExch(g.err, (int)SBGEMM_ERR_TIMEOUT);
+                }
+                bulk_wait_read();
+            }
+            __syncthreads();
+            if (s_fail) {
+                failed = true;
+                break;
+            }
+        } else {
+            __syncthreads();
+        }
 
         const S* st = stage_base + (it % stages) * stage_elems;
         const long long p0 = (long long)t * P;
@@ -246,14 +303,30 @@ pipe_kernel(Args<typename Cf::Ty> g)
                                   beta_zero, alpha_one, skip_ab, g.conja, g.conjb, sh);
         }
         // every thread is done reading this stage before it is refilled
+        // (and has ordered its output-tile writes before the bulk stores)
+        if constexpr (bulkC) {
+            if (!direct && fc) fence_proxy_async();
+        }
         __syncthreads();
-        if constexpr (ptr_form)
+        if constexpr (ptr_form) {
             store_ptrs<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(
                 const_cast<S* const*>(ptr_slot(it) + 2 * P), sOut, g.ldc, cnt);
-        else if (!direct)
-            store_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.C_, sOut, g.ldc2, g.ldc, p0, cnt, fc);
+        } else if (!direct) {
+            if (fc) store_flat<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT, bulkC>(g.C_, sOut, p0, cnt);
+            else store_operand<S, Cf::SC, Cf::SC_P, Cf::M, Cf::NT>(g.C_, sOut, g.ldc2, g.ldc, p0, cnt, false);
+        }
+    }
+    if constexpr (kBulk) {
+        if (failed) {
+            // let the copies already issued into this block's stages land (bounded)
+            for (int k = 0; k < stages; ++k) {
+                const long long tk = blockIdx.x + (long long)(it + k) * gridDim.x;
+                if (tk < ntiles) mbar_wait(&s_bar[(it + k) % stages], ((it + k) / stages) & 1);
+            }
+        }
     }
     cp_async_wait_dyn(0);
+    if constexpr (kBulk) bulk_wait_all();
 }
 
 // ------------------------------------------------------------ host launcher

@@ -95,3 +95,46 @@ def test_grouped_launch_configurations(cfg):
     for b, tA, tB, tC in keep:
         H.assert_parity(b, H.from_dev(tC, b.C)[0], H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5,
                         exact=True)
+
+
+def test_grouped_full_size_sampled():
+    """The benchmark's step at full size in its launch configuration: fp32,
+    m = 1..16 with N = 100,000 pairs each, op N/N, alpha = 1, beta = 0, one
+    grouped call (C starts as NaN, so a read of C would show), checked on a
+    sample of pairs of every size that the oracle computes one by one."""
+    N = 100_000
+    sizes = list(range(1, 17))
+    groups = (sbgemm.Group * len(sizes))()
+    keep = {}
+    for g, m in zip(groups, sizes):
+        S = m * m
+        A = inputs.draw("s", N * S, 1000 + m)
+        B = inputs.draw("s", N * S, 2000 + m)
+        tA, pA = H.to_dev(A)
+        tB, pB = H.to_dev(B)
+        tC = torch.full((N * S,), float("nan"), dtype=torch.float32, device=H.dev())
+        g.transa, g.transb, g.m, g.n, g.k = b"N", b"N", m, m, m
+        g.A, g.lda, g.lda2 = pA, m, S
+        g.B, g.ldb, g.ldb2 = pB, m, S
+        g.C, g.ldc, g.ldc2 = tC.data_ptr(), m, S
+        g.batchCount = N
+        keep[m] = (A, B, tA, tB, tC)
+    ab, bb = sbgemm._scalar_buf("s", 1.0), sbgemm._scalar_buf("s", 0.0)
+    s = torch.cuda.current_stream()
+    st = sbgemm.lib().sbgemm_gemm_grouped(0, ctypes.addressof(ab), ctypes.addressof(bb),
+                                          ctypes.addressof(groups), len(sizes), 0, s.cuda_stream)
+    assert st == 0, sbgemm.status_string(st)
+    s.synchronize()
+    for m in sizes:
+        A, B, tA, tB, tC = keep[m]
+        S = m * m
+        got = tC.cpu().numpy()
+        pick = np.unique((inputs.splitmix64(3000 + m, 256) % np.uint64(N)).astype(np.int64))
+        pick = np.concatenate([pick, [N - 1]])
+        sub = inputs.UniformBatch("s", "N", "N", m, m, m, pick.size, seed=0)
+        sub.A = A.reshape(N, S)[pick].ravel().copy()
+        sub.B = B.reshape(N, S)[pick].ravel().copy()
+        sub.C = np.full(pick.size * S, np.nan, dtype=np.float32)
+        ref = H.oracle_ref(sub, 1.0, 0.0)
+        H.assert_parity(sub, got.reshape(N, S)[pick].ravel().copy(), ref, 1.0, 0.0)
+        assert np.all(np.isfinite(got)), f"m={m}: an entry of C was not written"
