@@ -54,6 +54,21 @@ def test_uniform_inputs_within_bound(dtype, m):
         H.assert_parity(b, got, H.oracle_ref(b, alpha, beta), alpha, beta)
 
 
+@pytest.mark.parametrize("dtype", ["s", "c", "d"])
+@pytest.mark.parametrize("m", [11, 13, 14, 15])
+def test_bulk_copy_ragged_tails(dtype, m):
+    """Shapes staged by one bulk copy per operand and tile (large unpadded
+    matrices): batch sizes that end in a tile whose bytes are not a multiple
+    of 16 (the ragged end is copied with plain loads and stores), tiny
+    batches, C read (beta != 0) and not; bit-exact on small integers."""
+    alpha = 1.5
+    for N in (1, 2, 3, 5, 17, 257, 1001):
+        for beta in (0.0, -0.5):
+            b = inputs.UniformBatch(dtype, "N", "N", m, m, m, N, seed=7 * N + m, int_valued=True)
+            got = H.run_gpu(b, alpha, beta)
+            H.assert_parity(b, got, H.oracle_ref(b, alpha, beta), alpha, beta, exact=True)
+
+
 @pytest.mark.parametrize("dtype", ["s", "d", "c", "z"])
 @pytest.mark.parametrize("m", [5, 16])
 def test_all_nine_op_pairs_complex_scalars(dtype, m):
