@@ -412,8 +412,10 @@ sbgemm_status sbgemm_timer_destroy(sbgemm_timer timer);
 
 /*
  * Median time (ms) of `reps` calls of one kernel variant (host scalars).
- * When `flush` is not NULL, flush_bytes of it are overwritten before each
- * call (outside the timed interval) so every call starts with a cold L2.
+ * When `flush` is not NULL, flush_bytes of that device buffer (choose more
+ * than the L2 size) are read before each call, outside the timed interval:
+ * every call then starts with a cold L2 holding only clean lines (the
+ * previous call's results are written back before the timing starts).
  * Synchronises the stream.
  */
 sbgemm_status sbgemm_time_variant(int type, char transa, char transb, int m, int n, int k,

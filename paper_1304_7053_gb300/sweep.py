@@ -1,9 +1,11 @@
 """Throughput sweeps on the current GPU (timings only; correctness is the
 tests' job).
 
-Every timing is the median of `reps` calls, each preceded by an overwrite of
-a buffer larger than L2 so every call starts cold, measured with CUDA events
-(the library's timing core for this library's kernels).  The comparator is
+Every timing is the median of `reps` calls, each preceded by a read of a
+256 MB buffer (twice the L2): every call starts with a cold L2 that holds only
+clean lines, so the previous call's results are written back outside the
+timed interval.  Timed with CUDA events (the library's timing core for this
+library's kernels).  The comparator is
 cuBLAS strided-batched GEMM through torch.bmm on the same column-major data
 (C = A B column-major is C^T = B^T A^T row-major).
 
@@ -48,7 +50,13 @@ class Pools:
         self.A = torch.rand(n, device=dev, generator=g) * 2 - 1
         self.B = torch.rand(n, device=dev, generator=g) * 2 - 1
         self.C = torch.rand(n, device=dev, generator=g) * 2 - 1
-        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.flush = torch.ones(256 << 20, dtype=torch.uint8, device=dev)
+        self._sink = torch.empty((), dtype=torch.int64, device=dev)
+
+    def evict(self):
+        """Read the 256 MB flush buffer (L2 ends cold and clean)."""
+        torch = self.torch
+        self._sink = torch.sum(self.flush.view(torch.int32), dtype=torch.int64)
 
     def as_dtype(self, buf, dtype):
         torch = self.torch
@@ -90,7 +98,7 @@ def time_fn(pools, fn, reps):
     torch = pools.torch
     ts = []
     for _ in range(reps + 1):
-        pools.flush.fill_(1)
+        pools.evict()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         fn()
@@ -186,7 +194,7 @@ def time_cublas(pools, dtype, m, n, k, N, reps):
     C = pools.as_dtype(pools.C, dtype)[:N * m * n].view(N, n, m)   # row-major view of C^T
     ts = []
     for _ in range(reps + 1):
-        pools.flush.fill_(1)
+        pools.evict()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         torch.bmm(B, A, out=C)
