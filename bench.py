@@ -62,12 +62,17 @@ def paper_aggregate_gflops():
     return fl / t / 1e9
 
 
+# the sources the fp32 grouped kernel and its launch are built from
+GROUPED_SOURCES = ("grouped.cuh", "grouped_S.cu", "grouped_api.cu", "sbgemm_launch.cuh",
+                   "sbgemm_device.cuh", "tile_table.h")
+
+
 def kernel_source_hash():
+    """Hash of the grouped kernel's source files: recorded DRAM traffic is
+    reported only while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1304_7053_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if not fn.endswith((".cu", ".cuh", ".h")):
-            continue
+    for fn in GROUPED_SOURCES:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
