@@ -7,6 +7,11 @@ database keyed by device, shape and variant; a resumed run skips rows it
 already has.  The exhaustive choice per class is the fastest measured
 variant.
 
+The launch shapes of the batched paths are tuned the same way, exhaustively
+on the batch at hand: the bucketing window of a variable-size plan
+(``tune_vbatch``) and the grouped call's threads x stage bytes x depth
+(``tune_grouped``).
+
 The learned selector is a 3-layer perceptron (``sbgemm_mlp_*`` kernels,
 fp32) that maps problem features to one predicted log-time per variant.  It
 is trained on the database with the library's own forward, backward and Adam
@@ -153,6 +158,71 @@ class Tuner:
         return out
 
 
+# ---------------------------------------------------------------- launch-shape tuning
+
+def _time_calls(fn, reps: int, stream) -> float:
+    """Median CUDA-event time (ms) of fn() on `stream` after one warm call."""
+    import torch
+    ts = []
+    with torch.cuda.stream(stream):
+        fn()
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def tune_vbatch(dtype: str, problems, A, B, C, alpha=1.0, beta=1.0,
+                windows=(0, 262144, 65536, 16384), reps=5, stream=None):
+    """Exhaustive tuning of a variable-size batch's bucketing window: one
+    plan per window, `reps` timed runs each; the fastest window is installed
+    process-wide (``sbgemm_vbatch_config``) for the plans created after this
+    call.  Returns (best window, {window: ms}); window 0 is the whole batch.
+    C is overwritten by the trial runs."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    L = sbgemm.lib()
+    times = {}
+    try:
+        for w in windows:
+            L.sbgemm_vbatch_config(w)
+            plan = sbgemm.VPlan(dtype, problems)
+            try:
+                times[w] = _time_calls(lambda: plan.run(alpha, A, B, beta, C, stream=stream),
+                                       reps, stream)
+            finally:
+                plan.close()
+    finally:
+        L.sbgemm_vbatch_config(0)
+    best = min(times, key=times.get)
+    L.sbgemm_vbatch_config(best)
+    return best, times
+
+
+def tune_grouped(dtype: str, call, configs=None, reps=20, stream=None):
+    """Exhaustive tuning of the grouped launch configuration for one set of
+    batches: `call()` issues the grouped call on `stream`; every (threads,
+    stage bytes, stages) candidate is timed and the fastest is installed
+    (``sbgemm_grouped_config``).  Returns (best config, {config: ms})."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    if configs is None:
+        configs = [(t, sb, st) for t in (128, 256) for sb in (16384, 20480, 24576, 28672, 32768, 40960)
+                   for st in (2, 3) if st * sb + sb // 2 <= 220 * 1024]
+    times = {}
+    for cfg in configs:
+        sbgemm.grouped_config(dtype, *cfg)
+        times[cfg] = _time_calls(call, reps, stream)
+    best = min(times, key=times.get)
+    sbgemm.grouped_config(dtype, *best)
+    return best, times
+
+
 def random_classes(count: int, seed: int, dtypes=("s", "d", "c", "z", "h", "b"),
                    square_frac: float = 0.5):
     """Random problem classes: m, n, k in 1..16 (half of them square or one of
@@ -266,11 +336,16 @@ class CostModel:
         Y, _ = self.forward(X)
         return np.exp(Y.cpu().numpy().astype(np.float64) * self.sd + self.mu)
 
-    def choose(self, feats: np.ndarray, nvalid: np.ndarray) -> np.ndarray:
+    def choose(self, feats: np.ndarray, nvalid: np.ndarray, margin: float = 0.0) -> np.ndarray:
+        """The variant with the smallest predicted time, unless it is not
+        predicted to beat the default variant (0) by more than `margin`
+        (a fraction): then the default."""
         pred = self.predict_ms(feats)
         idx = np.arange(pred.shape[1])[None, :]
         pred = np.where(idx < nvalid[:, None], pred, np.inf)
-        return np.argmin(pred, axis=1)
+        best = np.argmin(pred, axis=1)
+        gain = pred[np.arange(len(best)), best] < pred[:, 0] * (1.0 - margin)
+        return np.where(gain, best, 0)
 
 
 def table_from_db(rows):
@@ -324,7 +399,14 @@ def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=3, steps=3000, db_p
     net = CostModel(seed=seed)
     hist = net.fit(Ftr, Ttr, steps=steps)
     t3 = _time.time()
-    chosen = net.choose(Fte, nvte)
+    # the trust margin is picked on the training classes only: the one whose
+    # choices give the smallest total training time
+    margins = (0.0, 0.02, 0.05, 0.1, 0.2)
+    tr_total = {mg: float(np.nansum(Ttr[np.arange(len(train)), net.choose(Ftr, nvtr, mg)]))
+                for mg in margins}
+    margin = min(margins, key=lambda mg: (tr_total[mg], mg))
+    chosen0 = net.choose(Fte, nvte, 0.0)
+    chosen = net.choose(Fte, nvte, margin)
     r_mlp = regret(Tte, chosen)
     r_def = regret(Tte, np.zeros(len(test), dtype=np.int64))
     multi = nvte > 1
@@ -342,6 +424,9 @@ def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=3, steps=3000, db_p
         "regret_default_mean_multi": float(r_def[multi].mean()) if multi.any() else 0.0,
         "mlp_picks_best": float((r_mlp == 0).mean()),
         "default_is_best": float((r_def == 0).mean()),
+        "trust_margin": margin,
+        "regret_mlp_no_margin_mean": float(regret(Tte, chosen0).mean()),
+        "time_mlp_no_margin_total_ms": float(Tte[np.arange(len(test)), chosen0].sum()),
         "time_mlp_total_ms": float(Tte[np.arange(len(test)), chosen].sum()),
         "time_default_total_ms": float(Tte[:, 0].sum()),
         "time_exhaustive_total_ms": float(np.nanmin(Tte, axis=1).sum()),

@@ -138,3 +138,33 @@ def test_grouped_full_size_sampled():
         ref = H.oracle_ref(sub, 1.0, 0.0)
         H.assert_parity(sub, got.reshape(N, S)[pick].ravel().copy(), ref, 1.0, 0.0)
         assert np.all(np.isfinite(got)), f"m={m}: an entry of C was not written"
+
+
+def test_tuned_grouped_config_installed_and_exact():
+    """The autotuner times the grouped call under each candidate launch
+    configuration, installs the fastest, and the call stays exact."""
+    from paper_1304_7053_gb300 import selector
+    specs = [("N", "N", s, s, s, 3000 + s, 0) for s in (2, 7, 12, 16)]
+    groups, keep = build("s", specs, True)
+    ab, bb = sbgemm._scalar_buf("s", 1.5), sbgemm._scalar_buf("s", -0.5)
+    s = torch.cuda.current_stream()
+
+    def call():
+        st = sbgemm.lib().sbgemm_gemm_grouped(0, ctypes.addressof(ab), ctypes.addressof(bb),
+                                              ctypes.addressof(groups), len(specs), 0,
+                                              s.cuda_stream)
+        assert st == 0
+
+    try:
+        cfgs = [(128, 16384, 2), (128, 28672, 2), (256, 32768, 2)]
+        best, times = selector.tune_grouped("s", call, configs=cfgs, reps=3, stream=s)
+        assert best in cfgs and times[best] == min(times.values())
+        for b, tA, tB, tC in keep:          # fresh C, then one call with the tuned launch
+            tC.copy_(torch.from_numpy(b.C.view(np.uint8)).cuda())
+        call()
+        s.synchronize()
+        for b, tA, tB, tC in keep:
+            H.assert_parity(b, H.from_dev(tC, b.C)[0], H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5,
+                            exact=True)
+    finally:
+        sbgemm.grouped_config("s")

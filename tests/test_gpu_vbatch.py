@@ -199,3 +199,21 @@ def test_million_problems_sampled():
     idx = np.concatenate([np.arange(o, o + s) for o, s in zip(desc[pick, 4], sizes)])
     sub[:, 4] = sub[:, 5] = sub[:, 6] = offs
     check("s", sub, A[idx], B[idx], C[idx], 1.0, 1.0, got[idx])
+
+
+def test_tuned_window_installed_and_exact():
+    """The autotuner times one plan per bucketing window, installs the
+    fastest, and plans built afterwards give the oracle's result."""
+    from paper_1304_7053_gb300 import selector
+    desc, la, lb, lc = inputs.vbatch_problems(30000, seed=5)
+    Ai, Bi, Ci = (inputs.draw("s", n, s, int_valued=True) for n, s in ((la, 31), (lb, 32), (lc, 33)))
+    tA, tB, tC = (torch.from_numpy(x).cuda() for x in (Ai, Bi, Ci))
+    try:
+        best, times = selector.tune_vbatch("s", sbgemm.vproblems_from_desc(desc), tA, tB, tC,
+                                           windows=(0, 4096, 1024), reps=3)
+        assert set(times) == {0, 4096, 1024} and best in times
+        assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+        got, _ = run_vbatch("s", desc, Ai, Bi, Ci, 1.5, -0.5)
+        check("s", desc, Ai, Bi, Ci, 1.5, -0.5, got, exact=True)
+    finally:
+        sbgemm.lib().sbgemm_vbatch_config(0)
