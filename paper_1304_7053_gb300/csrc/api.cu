@@ -85,9 +85,20 @@ int lookup_choice(int type, int m, int n, int k, int ta, int tb, int bz, int sc)
     return it == g_choice.end() ? -1 : it->second;
 }
 
-int variants_for(int m, int n, int k) {
+// the 16-bit types at m = n = k = 8 or 16 also have the tensor-core variant
+bool has_mma_variant(int type, int m, int n, int k) {
+    return (type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && m == n && n == k && (m == 8 || m == 16);
+}
+
+int variants_for(int type, int m, int n, int k) {
     if (m < 1 || n < 1 || k < 1 || m > 16 || n > 16 || k > 16) return 0;
-    return has_specialized(0, m, n, k) ? kNumPipeVariants + 1 : 1;
+    if (!has_specialized(0, m, n, k)) return 1;
+    return has_mma_variant(type, m, n, k) ? kMmaVariant + 1 : kNumPipeVariants + 1;
+}
+
+// the variant used when the selection table has no entry
+int default_variant(int type, int m, int n, int k) {
+    return has_mma_variant(type, m, n, k) ? kMmaVariant : 0;
 }
 
 // Map a public variant index to the internal one (generic kernel index =
@@ -166,14 +177,14 @@ sbgemm_status gemm_uniform(int type, char transa, char transb, int m, int n, int
     if (k == 0 || r.alpha_zero) return scale_typed(r);   // C = beta*C, A and B unread
     if (!A || !B) return SBGEMM_ERR_NULL_POINTER;
 
-    const int nv = variants_for(m, n, k);
+    const int nv = variants_for(type, m, n, k);
     if (variant >= 0) {
         if (variant >= nv) return SBGEMM_ERR_INVALID_VALUE;
     } else {
         variant = lookup_choice(type, m, n, k, r.ta, r.tb,
                                 scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
                                 size_class(batch));
-        if (variant < 0 || variant >= nv) variant = 0;
+        if (variant < 0 || variant >= nv) variant = default_variant(type, m, n, k);
     }
     r.variant = internal_variant(m, n, k, variant);
     return run_typed(r);
@@ -223,7 +234,7 @@ sbgemm_status gemm_nounif(int type, char transa, char transb, int m, int n, int 
     int variant = lookup_choice(type, m, n, k, r.ta, r.tb,
                                 scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
                                 size_class(batch));
-    if (variant < 0 || variant >= variants_for(m, n, k)) variant = 0;
+    if (variant < 0 || variant >= variants_for(type, m, n, k)) variant = default_variant(type, m, n, k);
     r.variant = internal_variant(m, n, k, variant);
     return run_typed(r);
 }
@@ -303,7 +314,7 @@ sbgemm_status sbgemm_Bgemm_multi_uniform_async(char transa, char transb, int m, 
 
 int sbgemm_num_variants(int type, int m, int n, int k) {
     if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return 0;
-    return sbg::variants_for(m, n, k);
+    return sbg::variants_for(type, m, n, k);
 }
 
 const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
@@ -311,7 +322,8 @@ const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
         "pipe tile16K st3 occ-max (st2 for fp64)", "pipe tile8K st4 occ-max",
         "pipe tile32K st2 occ-max", "pipe tile16K st3 1cta/sm (st2 for fp64)",
         "pipe tile4K st4 occ-max", "pipe tile24K st3 2cta/sm",
-        "generic thread-per-entry"};
+        "generic thread-per-entry",
+        "tensor-core mma.sync (16-bit, N/N, flat; else variant 0)"};
     const int nv = sbgemm_num_variants(type, m, n, k);
     if (variant < 0 || variant >= nv) return "invalid";
     return names[sbg::internal_variant(m, n, k, variant)];
@@ -329,7 +341,7 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
 sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
                                 int beta_zero, int size_class, int variant) {
     if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
-    const int nv = sbg::variants_for(m, n, k);
+    const int nv = sbg::variants_for(type, m, n, k);
     if (nv == 0 || variant >= nv || size_class < 0 || size_class > 7) return SBGEMM_ERR_INVALID_VALUE;
     std::lock_guard<std::mutex> lk(sbg::g_choice_mu);
     sbg::Key key(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
@@ -340,7 +352,7 @@ sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
 
 int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb, int beta_zero, int size_class) {
     const int v = sbg::lookup_choice(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
-    return v < 0 ? 0 : v;
+    return v < 0 ? sbg::default_variant(type, m, n, k) : v;
 }
 
 void sbgemm_clear_choices(void) {

@@ -12,6 +12,12 @@ SBG_DECL(S) SBG_DECL(D) SBG_DECL(C) SBG_DECL(Z) SBG_DECL(H) SBG_DECL(B)
 #define SBG_RUN(T)                                                         \
     sbgemm_status run_##T(const Req& r) {                                  \
         sbgemm_status st;                                                  \
+        if (r.variant == kMmaVariant) {                                    \
+            if (mma16_ok(r)) return run_mma16(r);                          \
+            Req r0 = r;                                                    \
+            r0.variant = 0;                                                \
+            return run_##T(r0);                                            \
+        }                                                                  \
         if (r.variant < kNumPipeVariants) {                                \
             if (run_##T##_part0(r, &st)) return st;                        \
             if (run_##T##_part1(r, &st)) return st;                        \

@@ -40,6 +40,12 @@ struct LaunchOpts {
 // shape is the generic runtime-size kernel (one thread per C entry, the
 // mapping of the paper's first method in Section 6).
 constexpr int kNumPipeVariants = 6;
+// Variant after the generic kernel: the tensor-core kernel of the 16-bit
+// types (csrc/mma16.cuh), for m = n = k = 8 or 16, op N/N, flat layouts; any
+// other request given this variant runs variant 0.
+constexpr int kMmaVariant = kNumPipeVariants + 1;
+sbgemm_status run_mma16(const Req& r);   // mma16.cu
+bool mma16_ok(const Req& r);
 inline LaunchOpts pipe_variant(int v, int type_code = 0) {
     // fp64 types are bound by the fp64 pipe, not by memory: two stages are
     // enough and leave room for more computing warps

@@ -240,6 +240,34 @@ def test_16bit_storage(dtype, m):
         H.assert_parity(b, got, H.oracle_ref(b, 1.5, beta), 1.5, beta)
 
 
+@pytest.mark.parametrize("dtype", ["h", "b"])
+@pytest.mark.parametrize("m", [8, 16])
+def test_tensor_core_variant(dtype, m):
+    """The mma.sync path of the 16-bit types (default for N/N flat m = 8, 16)
+    against the pipelined kernel's variant 0 and the oracle: ragged and tiny
+    batches (odd counts leave m = 8 with a half-used MMA), beta zero and not,
+    device scalars, and alpha = 0 with NaN in A and B (not read)."""
+    for N in (1, 2, 3, 31, 1001, 4099):
+        for beta in (0.0, -0.5):
+            b = inputs.UniformBatch(dtype, "N", "N", m, m, m, N, seed=3 * N + m)
+            ref = H.oracle_ref(b, 1.5, beta)
+            got7 = H.run_gpu(b, 1.5, beta, variant=7)
+            H.assert_parity(b, got7, ref, 1.5, beta)
+            got = H.run_gpu(b, 1.5, beta)            # the default: the same kernel
+            assert np.array_equal(got, got7)
+    b = inputs.UniformBatch(dtype, "N", "N", m, m, m, 777, seed=5)
+    H.assert_parity(b, H.run_gpu(b, 1.5, -0.5, device_scalars=True), H.oracle_ref(b, 1.5, -0.5),
+                    1.5, -0.5)
+    nan = {"h": 0x7E00, "b": 0x7FC0}[dtype]
+    A = np.full_like(b.A, nan)
+    B = np.full_like(b.B, nan)
+    got = H.run_gpu(b, 0.0, -0.5, A=A, B=B, device_scalars=True)
+    H.assert_parity(b, got, H.oracle_ref(b, 0.0, -0.5), 0.0, -0.5)
+    # a request the tensor-core kernel does not take runs variant 0
+    bt = inputs.UniformBatch(dtype, "T", "N", m, m, m, 500, seed=6)
+    H.assert_parity(bt, H.run_gpu(bt, 1.5, -0.5, variant=7), H.oracle_ref(bt, 1.5, -0.5), 1.5, -0.5)
+
+
 def test_quick_returns_leave_c_untouched():
     b = inputs.UniformBatch("s", "N", "N", 4, 4, 4, 10, seed=47)
     for (m, n, N) in ((0, 4, 10), (4, 0, 10), (4, 4, 0)):
