@@ -85,9 +85,10 @@ int lookup_choice(int type, int m, int n, int k, int ta, int tb, int bz, int sc)
     return it == g_choice.end() ? -1 : it->second;
 }
 
-// the 16-bit types at m = n = k = 8 or 16 also have the tensor-core variant
+// the 16-bit types at m = n = k = 8, 12 or 16 also have the tensor-core variant
 bool has_mma_variant(int type, int m, int n, int k) {
-    return (type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && m == n && n == k && (m == 8 || m == 16);
+    return (type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && m == n && n == k &&
+           (m == 8 || m == 12 || m == 16);
 }
 
 int variants_for(int type, int m, int n, int k) {

@@ -7,6 +7,7 @@ sbgemm_status run_mma16(const Req& r) {
     if (!mma16_eligible(r)) return SBGEMM_ERR_NOT_SUPPORTED;
     const bool b = r.type == SBGEMM_TYPE_B;
     if (r.m == 16) return b ? launch_mma16<TyB, 16>(r) : launch_mma16<TyH, 16>(r);
+    if (r.m == 12) return b ? launch_mma16<TyB, 12>(r) : launch_mma16<TyH, 12>(r);
     return b ? launch_mma16<TyB, 8>(r) : launch_mma16<TyH, 8>(r);
 }
 

@@ -1,5 +1,5 @@
 // Tensor-core kernel for 16-bit storage (binary16 / bfloat16 with fp32
-// accumulation), square m = n = k = 8 or 16, op N/N, flat batches.
+// accumulation), square m = n = k = 8, 12 or 16, op N/N, flat batches.
 //
 // Every pair's product is one or two warp-level mma.sync m16n8k16
 // operations (fp32 accumulators).  With column-major storage (Section 4),
@@ -9,6 +9,8 @@
 // are adjacent in memory (one 32-bit store each).
 //   m = 16: per pair, A operand = B^T (16 x 16), two n8 tiles of A^T,
 //           fragments loaded with ldmatrix (A^T with .trans).
+//   m = 12: as m = 16 on slots zero-padded to 16 x 16 (the padding adds
+//           zero terms; entries 12..15 of the result are not stored).
 //   m = 8:  two pairs per MMA, packed block-diagonally: A operand =
 //           diag(B0^T, B1^T) (16 x 16), B operand = [A0^T; A1^T] (16 x 8),
 //           result [C0^T; C1^T] (the off-diagonal fragment registers are 0).
@@ -85,13 +87,18 @@ struct MmaArgs {
     int beta_zero;             // host scalars: C not read
 };
 
+// shared-memory bytes of one matrix slot (m = 12 is padded to 16 x 16)
+__host__ __device__ constexpr int mma_slot_bytes(int m) { return m == 8 ? 128 : 512; }
+
 template <class Ty, int M>
 __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
 {
-    static_assert(M == 8 || M == 16, "tensor-core path for m = 8 and 16");
+    static_assert(M == 8 || M == 12 || M == 16, "tensor-core path for m = 8, 12 and 16");
     using S = typename Ty::S;
-    constexpr int SE = M * M;                  // elements per matrix
-    constexpr int CPM = SE * 2 / 16;           // 16-byte chunks per matrix
+    constexpr int SE = M * M;                  // elements per matrix in global memory
+    constexpr int CPM = SE * 2 / 16;           // 16-byte chunks per matrix (m = 8, 16)
+    constexpr bool kPad = M == 12;             // 12 x 12 computed as zero-padded 16 x 16
+    constexpr bool k16 = M != 8;               // one pair per two MMAs
     extern __shared__ __align__(16) unsigned char smem_raw[];
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -107,21 +114,32 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
     const int P = g.P, stages = g.stages;
     const long long batch = g.batch;
     const int ntiles = (int)((batch + P - 1) / P);
-    const int slot = SE * 2;                   // bytes per matrix slot
+    const int slot = mma_slot_bytes(M);        // bytes per matrix slot
     const int stage_bytes = P * slot * (has_cold ? 3 : 2);
     const S* gA = static_cast<const S*>(g.A);
     const S* gB = static_cast<const S*>(g.B);
     S* gC = static_cast<S*>(g.C);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // stage `cnt` pairs of one operand: 16-byte chunks, m = 16 slots swizzled
+    // stage `cnt` pairs of one operand: 16-byte chunks, 16 x 16 slots
+    // swizzled; m = 12 columns (24 bytes, 8-byte aligned) move as three
+    // 8-byte pieces into the first 12 entries of a slot row
     auto stage_op = [&](unsigned char* dst, const S* src, int cnt) {
         const char* s8 = reinterpret_cast<const char*>(src);
-        for (int c = tid; c < cnt * CPM; c += 128) {
-            const int q = c / CPM, lc = c - q * CPM;
-            int pos = lc;
-            if constexpr (M == 16) pos = mma_chunk16(lc >> 1, lc & 1);
-            cp_async16(dst + q * slot + pos * 16, s8 + 16 * (long long)c, 16);
+        if constexpr (kPad) {
+            for (int c = tid; c < cnt * 36; c += 128) {
+                const int q = c / 36, rem = c - q * 36;
+                const int l = rem / 3, pc = rem - 3 * l;
+                cp_async_elem<8>(dst + q * slot + 16 * mma_chunk16(l, pc >> 1) + 8 * (pc & 1),
+                                 s8 + 2 * ((long long)q * SE + 12 * l + 4 * pc));
+            }
+        } else {
+            for (int c = tid; c < cnt * CPM; c += 128) {
+                const int q = c / CPM, lc = c - q * CPM;
+                int pos = lc;
+                if constexpr (M == 16) pos = mma_chunk16(lc >> 1, lc & 1);
+                cp_async16(dst + q * slot + pos * 16, s8 + 16 * (long long)c, 16);
+            }
         }
     };
     auto issue = [&](int t, int s) {
@@ -135,6 +153,13 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
         if (!beta_zero) stage_op(st + 2 * P * slot, gC + p0 * SE, cnt);
     };
 
+    if constexpr (kPad) {
+        // the padding entries (rows and columns 12..15) are never staged:
+        // zero the whole pipeline once
+        for (int c = tid; c < stages * stage_bytes / 16; c += 128)
+            reinterpret_cast<uint4*>(smem_raw)[c] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+    }
     for (int s = 0; s < stages - 1; ++s) {
         const int t = blockIdx.x + s * gridDim.x;
         if (t < ntiles) issue(t, s);
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
         const long long p0 = (long long)t * P;
         const int cnt = (int)min((long long)P, batch - p0);
 
-        if constexpr (M == 16) {
+        if constexpr (k16) {
             for (int q = warp; q < cnt; q += 4) {
                 float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
                 if (!skip_ab) {
@@ -172,9 +197,11 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
                 S* cp = gC + (p0 + q) * SE;
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
+                    if (kPad && nt == 1 && tq >= 2) continue;   // i = 12..15: padding
 #pragma unroll
                     for (int hr = 0; hr < 2; ++hr) {       // rows gq and gq + 8 (columns j of C)
                         const int j = gq + 8 * hr;
+                        if (kPad && j >= 12) continue;
                         float x = d[nt][2 * hr], y = d[nt][2 * hr + 1];
                         if (!alpha_one) { x *= alpha; y *= alpha; }
                         if (!beta_zero) {
@@ -183,7 +210,7 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
                             x = fmaf(beta, o.x, x);
                             y = fmaf(beta, o.y, y);
                         }
-                        *reinterpret_cast<unsigned*>(cp + 8 * nt + 2 * tq + 16 * j) = pack2<Ty>(x, y);
+                        *reinterpret_cast<unsigned*>(cp + 8 * nt + 2 * tq + M * j) = pack2<Ty>(x, y);
                     }
                 }
             }
@@ -239,7 +266,7 @@ sbgemm_status launch_mma16(const Req& r) {
         g.beta = *static_cast<const float*>(r.beta);
         g.beta_zero = r.beta_zero;
     }
-    const int per_pair = M * M * 2 * (g.beta_zero ? 2 : 3);
+    const int per_pair = mma_slot_bytes(M) * (g.beta_zero ? 2 : 3);
     int P = (24 * 1024) / per_pair;
     P &= ~1;
     // at least two tiles per resident block when the batch is short
@@ -290,12 +317,12 @@ sbgemm_status launch_mma16(const Req& r) {
 }
 
 // true when the tensor-core kernel can run the request: 16-bit storage,
-// m = n = k = 8 or 16, op N/N, flat operands with 16-byte aligned bases
+// m = n = k = 8, 12 or 16, op N/N, flat operands with 16-byte aligned bases
 inline bool mma16_eligible(const Req& r) {
     if (r.type != SBGEMM_TYPE_H && r.type != SBGEMM_TYPE_B) return false;
     if (r.Cp || r.ta || r.tb) return false;
     const int m = r.m;
-    if (!(m == 8 || m == 16) || r.n != m || r.k != m) return false;
+    if (!(m == 8 || m == 12 || m == 16) || r.n != m || r.k != m) return false;
     const long long S = (long long)m * m;
     if (r.lda != m || r.ldb != m || r.ldc != m || r.lda2 != S || r.ldb2 != S || r.ldc2 != S) return false;
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };

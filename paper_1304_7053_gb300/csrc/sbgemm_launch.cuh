@@ -41,7 +41,7 @@ struct LaunchOpts {
 // mapping of the paper's first method in Section 6).
 constexpr int kNumPipeVariants = 6;
 // Variant after the generic kernel: the tensor-core kernel of the 16-bit
-// types (csrc/mma16.cuh), for m = n = k = 8 or 16, op N/N, flat layouts; any
+// types (csrc/mma16.cuh), for m = n = k = 8, 12 or 16, op N/N, flat layouts; any
 // other request given this variant runs variant 0.
 constexpr int kMmaVariant = kNumPipeVariants + 1;
 sbgemm_status run_mma16(const Req& r);   // mma16.cu

@@ -241,9 +241,9 @@ def test_16bit_storage(dtype, m):
 
 
 @pytest.mark.parametrize("dtype", ["h", "b"])
-@pytest.mark.parametrize("m", [8, 16])
+@pytest.mark.parametrize("m", [8, 12, 16])
 def test_tensor_core_variant(dtype, m):
-    """The mma.sync path of the 16-bit types (default for N/N flat m = 8, 16)
+    """The mma.sync path of the 16-bit types (default for N/N flat m = 8, 12, 16)
     against the pipelined kernel's variant 0 and the oracle: ragged and tiny
     batches (odd counts leave m = 8 with a half-used MMA), beta zero and not,
     device scalars, and alpha = 0 with NaN in A and B (not read)."""
