@@ -354,7 +354,7 @@ class CostModel:
 def default_choices(classes) -> np.ndarray:
     """The library's own choice for each class without a selection table
     (variant 0, or the tensor-core variant of the 16-bit types at m = n = k
-    = 8, 12, 16)."""
+    = 8, 16)."""
     sbgemm.clear_choices()
     return np.array([sbgemm.get_choice(c[0], c[1], c[2], c[3], c[4], c[5], c[7],
                                        size_class(c[8])) for c in classes], dtype=np.int64)
@@ -438,7 +438,7 @@ def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=3, steps=3000, db_p
         "mlp_picks_best": float((r_mlp == 0).mean()),
         "default_is_best": float((r_def == 0).mean()),
         "default_definition": "the library without a selection table (variant 0, or the "
-                              "tensor-core variant for 16-bit m = n = k = 8, 12, 16)",
+                              "tensor-core variant for 16-bit m = n = k = 8, 16)",
         "trust_margin": margin,
         "regret_mlp_no_margin_mean": float(regret(Tte, chosen0).mean()),
         "time_mlp_no_margin_total_ms": float(Tte[np.arange(len(test)), chosen0].sum()),

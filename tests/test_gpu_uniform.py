@@ -243,7 +243,8 @@ def test_16bit_storage(dtype, m):
 @pytest.mark.parametrize("dtype", ["h", "b"])
 @pytest.mark.parametrize("m", [8, 12, 16])
 def test_tensor_core_variant(dtype, m):
-    """The mma.sync path of the 16-bit types (default for N/N flat m = 8, 12, 16)
+    """The mma.sync path of the 16-bit types (variant 7; the default for N/N
+    flat m = 8, 16)
     against the pipelined kernel's variant 0 and the oracle: ragged and tiny
     batches (odd counts leave m = 8 with a half-used MMA), beta zero and not,
     device scalars, and alpha = 0 with NaN in A and B (not read)."""
@@ -253,8 +254,8 @@ def test_tensor_core_variant(dtype, m):
             ref = H.oracle_ref(b, 1.5, beta)
             got7 = H.run_gpu(b, 1.5, beta, variant=7)
             H.assert_parity(b, got7, ref, 1.5, beta)
-            got = H.run_gpu(b, 1.5, beta)            # the default: the same kernel
-            assert np.array_equal(got, got7)
+            if m != 12:                              # the default there: the same kernel
+                assert np.array_equal(H.run_gpu(b, 1.5, beta), got7)
     b = inputs.UniformBatch(dtype, "N", "N", m, m, m, 777, seed=5)
     H.assert_parity(b, H.run_gpu(b, 1.5, -0.5, device_scalars=True), H.oracle_ref(b, 1.5, -0.5),
                     1.5, -0.5)
