@@ -98,8 +98,8 @@ int variants_for(int type, int m, int n, int k) {
 }
 
 // the variant used when the selection table has no entry: the tensor-core
-// kernel at m = 8 and 16 (measured 1.3-1.7x faster); at m = 12 its 8-byte
-// staging into padded slots made it slower than the CUDA-core kernel
+// kernel at m = 8 and 16 (measured 1.3-1.7x faster); at m = 12 it measured
+// slower than the CUDA-core kernel (beta = 0) or equal (beta != 0)
 int default_variant(int type, int m, int n, int k) {
     return has_mma_variant(type, m, n, k) && m != 12 ? kMmaVariant : 0;
 }

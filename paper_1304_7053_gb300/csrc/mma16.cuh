@@ -9,8 +9,9 @@
 // are adjacent in memory (one 32-bit store each).
 //   m = 16: per pair, A operand = B^T (16 x 16), two n8 tiles of A^T,
 //           fragments loaded with ldmatrix (A^T with .trans).
-//   m = 12: as m = 16 on slots zero-padded to 16 x 16 (the padding adds
-//           zero terms; entries 12..15 of the result are not stored).
+//   m = 12: as m = 16 with zero fragments for rows and columns 12..15; the
+//           fragments come from 32-bit and 16-bit shared loads (24-byte
+//           columns give no 16-byte rows for ldmatrix).
 //   m = 8:  two pairs per MMA, packed block-diagonally: A operand =
 //           diag(B0^T, B1^T) (16 x 16), B operand = [A0^T; A1^T] (16 x 8),
 //           result [C0^T; C1^T] (the off-diagonal fragment registers are 0).
@@ -87,18 +88,16 @@ struct MmaArgs {
     int beta_zero;             // host scalars: C not read
 };
 
-// shared-memory bytes of one matrix slot (m = 12 is padded to 16 x 16)
-__host__ __device__ constexpr int mma_slot_bytes(int m) { return m == 8 ? 128 : 512; }
+// shared-memory bytes of one matrix slot (a matrix is stored contiguously)
+__host__ __device__ constexpr int mma_slot_bytes(int m) { return 2 * m * m; }
 
 template <class Ty, int M>
 __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
 {
     static_assert(M == 8 || M == 12 || M == 16, "tensor-core path for m = 8, 12 and 16");
     using S = typename Ty::S;
-    constexpr int SE = M * M;                  // elements per matrix in global memory
-    constexpr int CPM = SE * 2 / 16;           // 16-byte chunks per matrix (m = 8, 16)
-    constexpr bool kPad = M == 12;             // 12 x 12 computed as zero-padded 16 x 16
-    constexpr bool k16 = M != 8;               // one pair per two MMAs
+    constexpr int SE = M * M;                  // elements per matrix
+    constexpr int CPM = SE * 2 / 16;           // 16-byte chunks per matrix
     extern __shared__ __align__(16) unsigned char smem_raw[];
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -121,25 +120,17 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
     S* gC = static_cast<S*>(g.C);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // stage `cnt` pairs of one operand: 16-byte chunks, 16 x 16 slots
-    // swizzled; m = 12 columns (24 bytes, 8-byte aligned) move as three
-    // 8-byte pieces into the first 12 entries of a slot row
+    // stage `cnt` pairs of one operand: 16-byte chunks (a tile is one
+    // contiguous span); m = 16 slots swizzled
     auto stage_op = [&](unsigned char* dst, const S* src, int cnt) {
         const char* s8 = reinterpret_cast<const char*>(src);
-        if constexpr (kPad) {
-            for (int c = tid; c < cnt * 36; c += 128) {
-                const int q = c / 36, rem = c - q * 36;
-                const int l = rem / 3, pc = rem - 3 * l;
-                cp_async_elem<8>(dst + q * slot + 16 * mma_chunk16(l, pc >> 1) + 8 * (pc & 1),
-                                 s8 + 2 * ((long long)q * SE + 12 * l + 4 * pc));
-            }
-        } else {
-            for (int c = tid; c < cnt * CPM; c += 128) {
+        for (int c = tid; c < cnt * CPM; c += 128) {
+            int pos = c;
+            if constexpr (M == 16) {
                 const int q = c / CPM, lc = c - q * CPM;
-                int pos = lc;
-                if constexpr (M == 16) pos = mma_chunk16(lc >> 1, lc & 1);
-                cp_async16(dst + q * slot + pos * 16, s8 + 16 * (long long)c, 16);
+                pos = q * CPM + mma_chunk16(lc >> 1, lc & 1);
             }
+            cp_async16(dst + pos * 16, s8 + 16 * (long long)c, 16);
         }
     };
     auto issue = [&](int t, int s) {
@@ -153,13 +144,6 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
         if (!beta_zero) stage_op(st + 2 * P * slot, gC + p0 * SE, cnt);
     };
 
-    if constexpr (kPad) {
-        // the padding entries (rows and columns 12..15) are never staged:
-        // zero the whole pipeline once
-        for (int c = tid; c < stages * stage_bytes / 16; c += 128)
-            reinterpret_cast<uint4*>(smem_raw)[c] = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
-    }
     for (int s = 0; s < stages - 1; ++s) {
         const int t = blockIdx.x + s * gridDim.x;
         if (t < ntiles) issue(t, s);
@@ -182,7 +166,51 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
         const long long p0 = (long long)t * P;
         const int cnt = (int)min((long long)P, batch - p0);
 
-        if constexpr (k16) {
+        if constexpr (M == 12) {
+            // 12 x 12 pairs computed as 16 x 16 with zero fragments outside:
+            // the 24-byte columns leave no 16-byte rows for ldmatrix, so the
+            // fragments are read as 32-bit pairs (B^T rows are contiguous)
+            // and 16-bit entries (A^T: two columns of A per register)
+            for (int q = warp; q < cnt; q += 4) {
+                const unsigned short* Bs = reinterpret_cast<const unsigned short*>(st + P * slot + q * slot);
+                const unsigned short* As = reinterpret_cast<const unsigned short*>(st + q * slot);
+                auto fragB = [&](int j, int l) -> unsigned {          // B^T(j, l), B^T(j, l + 1)
+                    return (j < 12 && l < 12) ? *reinterpret_cast<const unsigned*>(Bs + l + 12 * j) : 0u;
+                };
+                auto fragA = [&](int i, int l) -> unsigned {          // A^T(l, i), A^T(l + 1, i)
+                    return (i < 12 && l < 12) ? (unsigned)As[i + 12 * l] | ((unsigned)As[i + 12 * (l + 1)] << 16)
+                                              : 0u;
+                };
+                float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                if (!skip_ab) {
+                    const unsigned a[4] = {fragB(gq, 2 * tq), fragB(gq + 8, 2 * tq), fragB(gq, 2 * tq + 8),
+                                           fragB(gq + 8, 2 * tq + 8)};
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+                        mma16816<Ty>(d[nt], a, fragA(8 * nt + gq, 2 * tq), fragA(8 * nt + gq, 2 * tq + 8));
+                }
+                S* cp = gC + (p0 + q) * SE;
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    if (nt == 1 && tq >= 2) continue;       // i = 12..15: outside the matrix
+#pragma unroll
+                    for (int hr = 0; hr < 2; ++hr) {
+                        const int j = gq + 8 * hr;
+                        if (j >= 12) continue;
+                        const int i = 8 * nt + 2 * tq;
+                        float x = d[nt][2 * hr], y = d[nt][2 * hr + 1];
+                        if (!alpha_one) { x *= alpha; y *= alpha; }
+                        if (!beta_zero) {
+                            const float2 o = unpack2<Ty>(*reinterpret_cast<const unsigned*>(
+                                sC + q * slot + 2 * (i + 12 * j)));
+                            x = fmaf(beta, o.x, x);
+                            y = fmaf(beta, o.y, y);
+                        }
+                        *reinterpret_cast<unsigned*>(cp + i + 12 * j) = pack2<Ty>(x, y);
+                    }
+                }
+            }
+        } else if constexpr (M == 16) {
             for (int q = warp; q < cnt; q += 4) {
                 float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
                 if (!skip_ab) {
@@ -197,11 +225,9 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
                 S* cp = gC + (p0 + q) * SE;
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
-                    if (kPad && nt == 1 && tq >= 2) continue;   // i = 12..15: padding
 #pragma unroll
                     for (int hr = 0; hr < 2; ++hr) {       // rows gq and gq + 8 (columns j of C)
                         const int j = gq + 8 * hr;
-                        if (kPad && j >= 12) continue;
                         float x = d[nt][2 * hr], y = d[nt][2 * hr + 1];
                         if (!alpha_one) { x *= alpha; y *= alpha; }
                         if (!beta_zero) {
@@ -210,7 +236,7 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
                             x = fmaf(beta, o.x, x);
                             y = fmaf(beta, o.y, y);
                         }
-                        *reinterpret_cast<unsigned*>(cp + 8 * nt + 2 * tq + M * j) = pack2<Ty>(x, y);
+                        *reinterpret_cast<unsigned*>(cp + 8 * nt + 2 * tq + 16 * j) = pack2<Ty>(x, y);
                     }
                 }
             }
