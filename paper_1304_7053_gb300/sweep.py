@@ -19,7 +19,9 @@ N = 1e5), one A shared by all pairs (lda2 = 0, N = 1e6; algorithmic bytes
 count B and C only), and 16-bit storage (binary16/bfloat16, m in
 {8, 12, 16}, N = 1e6).  ``grouped_config`` (only when named) sweeps the
 launch configuration of the grouped call on the fp32 and fp64 sizes 1..16
-workload.
+workload; ``once`` (only when named) makes one untimed call per type and
+size (fp32 and fp64, m = 8..16, N = 1e5, op N/N, alpha = 1, beta = 0, L2
+evicted before each): the launches a kernel-level profile reads.
 """
 from __future__ import annotations
 
@@ -233,7 +235,7 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
     ap.add_argument("--sections", default="fixed,ops,fem,interface,shared_a,16bit",
                     help="comma-separated subset of the sections to run "
-                         "(grouped_config runs only when named)")
+                         "(grouped_config and once run only when named)")
     args = ap.parse_args(argv)
     want = set(args.sections.split(","))
     import torch
@@ -249,6 +251,21 @@ def main(argv=None):
                 rows.append(r)
                 print(json.dumps(r), flush=True)
         want.discard("grouped_config")
+        if not want:
+            with open(args.out, "w") as f:
+                json.dump(rows, f)
+            return rows
+    if "once" in want:
+        pools = Pools(8 * 256 * 100_000 + 4096, dev)
+        for dtype in ("s", "d"):
+            for m in range(8, 17):
+                S = m * m
+                pools.evict()
+                sbgemm.gemm_multi_uniform(dtype, "N", "N", m, m, m, 1.0, pools.A.data_ptr(), m, S,
+                                          pools.B.data_ptr(), m, S, 0.0, pools.C.data_ptr(), m, S,
+                                          100_000)
+        torch.cuda.synchronize()
+        want.discard("once")
         if not want:
             with open(args.out, "w") as f:
                 json.dump(rows, f)

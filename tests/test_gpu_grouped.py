@@ -168,3 +168,40 @@ def test_tuned_grouped_config_installed_and_exact():
                             exact=True)
     finally:
         sbgemm.grouped_config("s")
+
+
+@pytest.mark.parametrize("dtype", ["s", "d", "c", "b"])
+@pytest.mark.parametrize("beta", [0.0, -0.5])
+def test_grouped_sizes_off_the_16_byte_grid(dtype, beta):
+    """Sizes whose matrices are not a whole number of 16-byte chunks (tiles
+    a multiple of 2-8 pairs, a ragged last tile whose final chunk is
+    partial): results match the oracle and the bytes around every C stay
+    untouched."""
+    int_valued = dtype in "sdc"
+    sizes = list(range(1, 17, 2)) + [6, 10, 14]
+    groups = (sbgemm.Group * len(sizes))()
+    keep = []
+    guard_front, guard_back = 32, 48
+    for g, m in zip(groups, sizes):
+        N = 1000 + 37 * m
+        b = inputs.UniformBatch(dtype, "N", "N", m, m, m, N, seed=11 * m, int_valued=int_valued)
+        tA, pA = H.to_dev(b.A)
+        tB, pB = H.to_dev(b.B)
+        tC, pC = H.to_dev(b.C, pad_front=guard_front, pad_back=guard_back)
+        g.transa, g.transb, g.m, g.n, g.k = b"N", b"N", m, m, m
+        g.A, g.lda, g.lda2 = pA, m, m * m
+        g.B, g.ldb, g.ldb2 = pB, m, m * m
+        g.C, g.ldc, g.ldc2 = pC, m, m * m
+        g.batchCount = N
+        keep.append((b, tA, tB, tC))
+    ab, bb = sbgemm._scalar_buf(dtype, 1.5), sbgemm._scalar_buf(dtype, beta)
+    s = torch.cuda.current_stream()
+    st = sbgemm.lib().sbgemm_gemm_grouped(sbgemm.TYPE_CODES[dtype], ctypes.addressof(ab),
+                                          ctypes.addressof(bb), ctypes.addressof(groups),
+                                          len(sizes), 0, s.cuda_stream)
+    assert st == 0, sbgemm.status_string(st)
+    s.synchronize()
+    for b, tA, tB, tC in keep:
+        got, raw = H.from_dev(tC, b.C, pad_front=guard_front)
+        assert np.all(raw[:guard_front] == 0x5A) and np.all(raw[guard_front + b.C.nbytes:] == 0x5A)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, beta), 1.5, beta, exact=int_valued)
