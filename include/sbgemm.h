@@ -292,6 +292,9 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
  * sbgemm_get_choice returns the installed or default variant.  The table is
  * process-wide host state; set it before issuing work, not concurrently with
  * calls that read it.  size_class = floor(log10(batchCount)) clamped to 0..7.
+ * Default without an entry: the tensor-core variant (7) for the 16-bit types
+ * at m = n = k = 8 and 16; variant 2 for complex64, and for fp32 with
+ * size_class <= 5; variant 0 otherwise.
  */
 sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
                                 int beta_zero, int size_class, int variant);
@@ -411,7 +414,10 @@ sbgemm_status sbgemm_timer_elapsed(sbgemm_timer timer, int from, int to, float* 
 sbgemm_status sbgemm_timer_destroy(sbgemm_timer timer);
 
 /*
- * Median time (ms) of `reps` calls of one kernel variant (host scalars).
+ * Time (ms) of one call of a kernel variant (host scalars): the mean over
+ * `reps` calls, each timed alone with CUDA events, of those within 2 us of
+ * the median (event timestamps can advance in steps of about 1 us; the mean
+ * of many calls resolves below a step).
  * When `flush` is not NULL, flush_bytes of that device buffer (choose more
  * than the L2 size) are read before each call, outside the timed interval:
  * every call then starts with a cold L2 holding only clean lines (the
@@ -461,9 +467,13 @@ sbgemm_status sbgemm_mlp_backward(int F, int H, int V, const float* params, cons
 
 /* One Adam step (Kingma & Ba 2015, Algorithm 1) on n parameters; t >= 1 is
  * the step number used in the bias corrections; m, v are the moment
- * buffers (zero before the first step). */
+ * buffers (zero before the first step).  l2 >= 0 adds an L2 penalty
+ * (l2 / 2) |params|^2 to the loss: the step uses g = grads + l2 * params in
+ * place of grads (0 gives plain Adam; negative or non-finite l2 is
+ * SBGEMM_ERR_INVALID_VALUE). */
 sbgemm_status sbgemm_mlp_adam(long long n, float* params, const float* grads, float* m, float* v,
-                              int t, float lr, float beta1, float beta2, float eps, void* stream);
+                              int t, float lr, float beta1, float beta2, float eps, float l2,
+                              void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Status.                                                              */

@@ -74,15 +74,18 @@ def backward(p: dict, cache, Y: np.ndarray, T: np.ndarray, mask: np.ndarray) -> 
 
 
 def adam_step(p: dict, g: dict, state: dict, lr: float, beta1: float = 0.9,
-              beta2: float = 0.999, eps: float = 1e-8) -> None:
-    """One Adam update in place.  ``state`` holds t and the moment estimates."""
+              beta2: float = 0.999, eps: float = 1e-8, l2: float = 0.0) -> None:
+    """One Adam update in place.  ``state`` holds t and the moment estimates.
+    ``l2``: an L2 penalty (l2 / 2) |p|^2 added to the loss, so the moments
+    see the gradient g + l2 * p."""
     t = state.get("t", 0) + 1
     state["t"] = t
     for name in PARAM_NAMES:
         m = state.setdefault("m_" + name, np.zeros_like(p[name]))
         v = state.setdefault("v_" + name, np.zeros_like(p[name]))
-        m[...] = beta1 * m + (1.0 - beta1) * g[name]
-        v[...] = beta2 * v + (1.0 - beta2) * g[name] * g[name]
+        gt = g[name] + l2 * p[name]
+        m[...] = beta1 * m + (1.0 - beta1) * gt
+        v[...] = beta2 * v + (1.0 - beta2) * gt * gt
         mhat = m / (1.0 - beta1 ** t)
         vhat = v / (1.0 - beta2 ** t)
         p[name] = p[name] - lr * mhat / (np.sqrt(vhat) + eps)

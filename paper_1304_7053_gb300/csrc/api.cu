@@ -97,11 +97,23 @@ int variants_for(int type, int m, int n, int k) {
     return has_mma_variant(type, m, n, k) ? kMmaVariant + 1 : kNumPipeVariants + 1;
 }
 
-// the variant used when the selection table has no entry: the tensor-core
-// kernel at m = 8 and 16 (measured 1.3-1.7x faster); at m = 12 it measured
-// slower than the CUDA-core kernel (beta = 0) or equal (beta != 0)
-int default_variant(int type, int m, int n, int k) {
-    return has_mma_variant(type, m, n, k) && m != 12 ? kMmaVariant : 0;
+// The variant used when the selection table has no entry (sc: the batch's
+// size class, floor(log10 N)):
+// - the tensor-core kernel for the 16-bit types at m = n = k = 8 and 16
+//   (measured 1.3-1.7x faster; at m = 12 it measured slower than the
+//   CUDA-core kernel with beta = 0 and equal otherwise);
+// - variant 2 (32 KB tiles, two stages: more blocks per SM and a shorter
+//   pipeline to fill) for complex64 and for fp32 below 1e6 pairs: over the
+//   square N/N sizes 2..16 it took 9% less total time than variant 0 for
+//   complex64 at N = 1e5 and 1e6, and 5% less for fp32 at N = 1e5 (up to 20%
+//   per size), while fp32 at N = 1e6 measured the same total;
+// - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
+//   no difference; the 16-bit CUDA-core kernels were mixed).
+int default_variant(int type, int m, int n, int k, int sc) {
+    if (has_mma_variant(type, m, n, k) && m != 12) return kMmaVariant;
+    if (!has_specialized(0, m, n, k)) return 0;
+    if (type == SBGEMM_TYPE_C || (type == SBGEMM_TYPE_S && sc <= 5)) return 2;
+    return 0;
 }
 
 // Map a public variant index to the internal one (generic kernel index =
@@ -187,7 +199,7 @@ sbgemm_status gemm_uniform(int type, char transa, char transb, int m, int n, int
         variant = lookup_choice(type, m, n, k, r.ta, r.tb,
                                 scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
                                 size_class(batch));
-        if (variant < 0 || variant >= nv) variant = default_variant(type, m, n, k);
+        if (variant < 0 || variant >= nv) variant = default_variant(type, m, n, k, size_class(batch));
     }
     r.variant = internal_variant(m, n, k, variant);
     return run_typed(r);
@@ -237,7 +249,8 @@ sbgemm_status gemm_nounif(int type, char transa, char transb, int m, int n, int 
     int variant = lookup_choice(type, m, n, k, r.ta, r.tb,
                                 scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
                                 size_class(batch));
-    if (variant < 0 || variant >= variants_for(type, m, n, k)) variant = default_variant(type, m, n, k);
+    if (variant < 0 || variant >= variants_for(type, m, n, k))
+        variant = default_variant(type, m, n, k, size_class(batch));
     r.variant = internal_variant(m, n, k, variant);
     return run_typed(r);
 }
@@ -355,7 +368,7 @@ sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
 
 int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb, int beta_zero, int size_class) {
     const int v = sbg::lookup_choice(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
-    return v < 0 ? sbg::default_variant(type, m, n, k) : v;
+    return v < 0 ? sbg::default_variant(type, m, n, k, size_class) : v;
 }
 
 void sbgemm_clear_choices(void) {

@@ -6,7 +6,9 @@
 //   Y  = H2 W3^T + b3
 //   L  = sum mask (Y - T)^2 / (2 M),  M = sum mask
 // Gradients are the chain rule layer by layer (relu'(0) = 0); the update is
-// Adam (Kingma & Ba, ICLR 2015, Algorithm 1).  Every reduction is a plain
+// Adam (Kingma & Ba, ICLR 2015, Algorithm 1) on the gradient of
+// L + (l2 / 2) |params|^2 (an L2 penalty on every parameter, added to the
+// gradient before the moment estimates).  Every reduction is a plain
 // loop in a fixed order (no atomics), so results are reproducible.
 //
 // Parameters live in one buffer: W1 (H x F), b1 (H), W2 (H x H), b2 (H),
@@ -117,10 +119,10 @@ __global__ void dense_bwd_x(const float* __restrict__ dZ, const float* __restric
 
 __global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, float lr, float b1,
-                            float b2, float eps, float c1, float c2) {
+                            float b2, float eps, float l2, float c1, float c2) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float gi = g[i];
+    const float gi = g[i] + l2 * p[i];      // gradient of L + (l2 / 2) |p|^2
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -189,8 +191,9 @@ sbgemm_status sbgemm_mlp_backward(int F, int H, int V, const float* params, cons
 }
 
 sbgemm_status sbgemm_mlp_adam(long long n, float* params, const float* grads, float* m, float* v,
-                              int t, float lr, float beta1, float beta2, float eps, void* stream) {
-    if (n < 0 || t < 1) return SBGEMM_ERR_INVALID_VALUE;
+                              int t, float lr, float beta1, float beta2, float eps, float l2,
+                              void* stream) {
+    if (n < 0 || t < 1 || !(l2 >= 0.f) || l2 > 1e30f) return SBGEMM_ERR_INVALID_VALUE;
     if (n == 0) return SBGEMM_SUCCESS;
     if (!params || !grads || !m || !v) return SBGEMM_ERR_NULL_POINTER;
     // bias corrections 1 - beta^t, computed on the host in double
@@ -199,7 +202,7 @@ sbgemm_status sbgemm_mlp_adam(long long n, float* params, const float* grads, fl
     c1 -= p1;
     c2 -= p2;
     adam_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, params, grads, m, v, lr, beta1,
-                                                                 beta2, eps, (float)c1, (float)c2);
+                                                                 beta2, eps, l2, (float)c1, (float)c2);
     return (sbgemm_status)cudaGetLastError();
 }
 

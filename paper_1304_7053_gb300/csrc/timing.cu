@@ -84,6 +84,21 @@ __global__ void flush_read_kernel(const uint4* __restrict__ p, size_t n, unsigne
     if (acc == 0x9E3779B9u && sink) *sink = acc;
 }
 
+// Event timestamps can advance in steps of about a microsecond, and where a
+// call starts against those steps varies from call to call, so the mean of
+// the calls resolves a time below one step where the median snaps to a
+// step.  Calls more than 2 us from the median (delayed or preempted) are
+// left out.
+float robust_mean_ms(std::vector<float> d) {
+    std::sort(d.begin(), d.end());
+    const float med = d[d.size() / 2];
+    double sum = 0.0;
+    int n = 0;
+    for (float x : d)
+        if (x >= med - 0.002f && x <= med + 0.002f) { sum += x; ++n; }
+    return (float)(sum / n);
+}
+
 }  // namespace
 
 extern "C" {
@@ -95,8 +110,14 @@ sbgemm_status sbgemm_time_variant(int type, char transa, char transb, int m, int
     void* stream, float* ms_out) {
     if (!ms_out || reps < 1 || reps > 100000 || variant < 0) return SBGEMM_ERR_INVALID_VALUE;
     cudaStream_t s = (cudaStream_t)stream;
+    // one untimed call first: the first launch of a variant does host-side
+    // set-up (function attributes, occupancy) while the GPU waits
+    sbgemm_status st = sbg::gemm_uniform(type, transa, transb, m, n, k, alpha, A, lda, lda2, B,
+                                         ldb, ldb2, beta, C, ldc, ldc2, batchCount,
+                                         SBGEMM_SCALARS_HOST, variant, s);
+    if (st != SBGEMM_SUCCESS) return st;
     sbgemm_timer t = nullptr;
-    sbgemm_status st = sbgemm_timer_create(&t, 2 * reps);
+    st = sbgemm_timer_create(&t, 2 * reps);
     if (st != SBGEMM_SUCCESS) return st;
     for (int r = 0; r < reps && st == SBGEMM_SUCCESS; ++r) {
         if (flush && flush_bytes >= 16) {
@@ -121,8 +142,7 @@ sbgemm_status sbgemm_time_variant(int type, char transa, char transb, int m, int
     }
     sbgemm_timer_destroy(t);
     if (st != SBGEMM_SUCCESS) return st;
-    std::sort(d.begin(), d.end());
-    *ms_out = d[d.size() / 2];
+    *ms_out = robust_mean_ms(d);
     return SBGEMM_SUCCESS;
 }
 

@@ -73,7 +73,7 @@ SIGNATURES = {
     "sbgemm_mlp_backward": (_i, [_i, _i, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                  _vp]),
     "sbgemm_mlp_adam": (_i, [_ll, _vp, _vp, _vp, _vp, _i, ctypes.c_float, ctypes.c_float,
-                             ctypes.c_float, ctypes.c_float, _vp]),
+                             ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
     "sbgemm_status_string": (ctypes.c_char_p, [_i]),
     "sbgemm_version": (_i, []),
 }

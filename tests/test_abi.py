@@ -104,11 +104,20 @@ def test_variant_table_host_logic():
     assert sbgemm.num_variants("h", 10, 10, 10) == 7
     assert "tensor-core" in sbgemm.variant_name("h", 16, 16, 16, 7)
     sbgemm.clear_choices()
-    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 0
+    # defaults without a table entry: 32 KB two-stage tiles (variant 2) for
+    # fp32 below 1e6 pairs and for complex64, the tensor cores for 16-bit
+    # m = 8, 16, variant 0 elsewhere, the generic kernel (0) off the table
+    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 2
+    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 6) == 0
+    assert sbgemm.get_choice("c", 10, 10, 10, 0, 0, 1, 6) == 2
+    assert sbgemm.get_choice("d", 10, 10, 10, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("h", 16, 16, 16, 0, 0, 1, 6) == 7
+    assert sbgemm.get_choice("h", 12, 12, 12, 0, 0, 1, 6) == 0
+    assert sbgemm.get_choice("s", 7, 3, 11, 0, 0, 1, 5) == 0
     sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, 3)
     assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 3
     sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, -1)
-    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 2
     with pytest.raises(sbgemm.SbgemmError):
         sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, 99)
     sbgemm.clear_choices()
@@ -147,3 +156,18 @@ def test_vbatch_window_config_validation():
     assert L.sbgemm_vbatch_config(-1) == -5   # SBGEMM_ERR_INVALID_VALUE
     assert L.sbgemm_vbatch_config(65536) == 0
     assert L.sbgemm_vbatch_config(0) == 0
+
+
+def test_mlp_adam_argument_errors():
+    """Host-only: the Adam step rejects a negative or non-finite L2 penalty
+    and a step number below 1 before touching the device."""
+    L = sbgemm.lib()
+    args = dict(lr=1e-3, b1=0.9, b2=0.999, eps=1e-8)
+    call = lambda t, l2, ptr: L.sbgemm_mlp_adam(4, ptr, ptr, ptr, ptr, t, args["lr"], args["b1"],
+                                                 args["b2"], args["eps"], l2, None)
+    assert call(1, -1.0, None) == -5
+    assert call(1, float("nan"), None) == -5
+    assert call(1, float("inf"), None) == -5
+    assert call(0, 0.0, None) == -5
+    assert call(1, 0.0, None) == -4       # valid penalty, missing buffers
+    assert L.sbgemm_mlp_adam(0, None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-8, 5e-3, None) == 0

@@ -83,6 +83,29 @@ def test_adam_closed_form_two_steps():
     assert st["t"] == 2
 
 
+def test_adam_l2_penalty_closed_form():
+    """With an L2 penalty (l2 / 2) p^2 the first step is the sign step of
+    Algorithm 1 on g + l2 * p: theta -= lr * (g + l2 p) / (|g + l2 p| + eps);
+    a gradient that the penalty exactly cancels leaves p in place, and
+    l2 = 0 is plain Adam."""
+    lr, eps, l2 = 0.01, 1e-8, 0.5
+    p = {n: np.array([0.5]) for n in mlp.PARAM_NAMES}
+    g = {n: np.array([-0.1]) for n in mlp.PARAM_NAMES}
+    mlp.adam_step(p, g, {}, lr, 0.9, 0.999, eps, l2=l2)
+    ge = -0.1 + l2 * 0.5
+    assert p["W2"][0] == pytest.approx(0.5 - lr * ge / (abs(ge) + eps), abs=1e-15)
+    p = {n: np.array([0.4]) for n in mlp.PARAM_NAMES}
+    g = {n: np.array([-0.2]) for n in mlp.PARAM_NAMES}      # g + l2 p = 0
+    mlp.adam_step(p, g, {}, lr, 0.9, 0.999, eps, l2=l2)
+    assert p["b1"][0] == 0.4
+    p0 = {n: np.array([0.3]) for n in mlp.PARAM_NAMES}
+    p1 = {n: np.array([0.3]) for n in mlp.PARAM_NAMES}
+    gz = {n: np.array([0.7]) for n in mlp.PARAM_NAMES}
+    mlp.adam_step(p0, gz, {}, lr)
+    mlp.adam_step(p1, gz, {}, lr, l2=0.0)
+    assert p0["W3"][0] == p1["W3"][0]
+
+
 def test_training_reduces_loss():
     """A few hundred full-batch Adam steps fit a smooth target."""
     F, H, V, B = 4, 16, 3, 64
