@@ -34,21 +34,24 @@ constexpr int kVKinds = 17;
 constexpr int kVGeneric = 16;
 constexpr int kVThreads = 128;
 constexpr int kVMaxTile = 128;
-constexpr int kVBlocksPerSM = 2;
 // problems per bucketing window of a plan: by default the whole batch, so
 // each bucket's tiles are contiguous in the queue and all blocks run the
 // same size-specialised code at once (windows of 4096 problems made the
 // blocks switch kinds nearly every tile: 1.8x slower on the fp32 mix)
 constexpr int kVDefaultWindow = 1 << 30;
 
-// Pipeline shape per storage type.  Memory-bound types keep two tiles of
-// 24 KB in flight; fp64 and complex128, bound by the fp64 pipe, take 48 KB
-// stages (more matrices per compute round) with one tile in flight.
-// Shared memory: stages x stage bytes + (2 stages - 1) record buffers of
-// kVMaxTile records, two blocks per SM either way.
+// Pipeline shape per storage type: two stages (one tile in flight while
+// another computes).  Memory-bound types take 28 KB stages and three blocks
+// of 128 threads per SM (a cap of 168 registers); fp64 and complex128, bound
+// by the fp64 pipe, 48 KB stages (more matrices per compute round) and two
+// blocks.  Three stages of 24 KB with two blocks per SM measured 0.259 ms on
+// the fp32 mix against 0.213 ms for this shape, four blocks of 20 KB stages
+// 0.241 ms.  Shared memory: stages x stage bytes + (2 stages - 1) record
+// buffers of kVMaxTile records + the tile descriptors.
 __host__ __device__ constexpr bool vfp64(int type) { return type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z; }
-__host__ __device__ constexpr int vstages_of(int type) { return vfp64(type) ? 2 : 3; }
-__host__ __device__ constexpr int vstage_bytes_of(int type) { return vfp64(type) ? 48 * 1024 : 24 * 1024; }
+__host__ __device__ constexpr int vstages_of(int) { return 2; }
+__host__ __device__ constexpr int vstage_bytes_of(int type) { return vfp64(type) ? 48 * 1024 : 28 * 1024; }
+__host__ __device__ constexpr int vblocks_of(int type) { return vfp64(type) ? 2 : 3; }
 __host__ __device__ constexpr int vrec_slots_of(int type) { return 2 * vstages_of(type) - 1; }
 __host__ __device__ constexpr int vitem_slots_of(int type) { return 3 * vstages_of(type) - 2; }
 
@@ -328,7 +331,7 @@ __device__ __forceinline__ void vcompute_store_kind(int kind, typename Ty::S* st
 }
 
 template <class Ty>
-__global__ void __launch_bounds__(kVThreads, kVBlocksPerSM) vbatch_kernel(VArgs<Ty> g)
+__global__ void __launch_bounds__(kVThreads, vblocks_of(Ty::code)) vbatch_kernel(VArgs<Ty> g)
 {
     // Software pipeline of one block over the tiles it takes from the queue
     // (its j-th tile is "tile j"; D = pipeline stages).  Every tile needs, in order:
