@@ -13,7 +13,9 @@ cuBLAS strided-batched GEMM through torch.bmm on the same column-major data
 
     python -m paper_1304_7053_gb300.sweep --out sweep.json [--quick]
 
-Sections: the fixed-size sweep (S/D/C/Z, m = 1..16, N = 1e3/1e5/1e6,
+Sections: the small configuration (fp32, m = 10, N = 1e4: cold and hot,
+direct and CUDA-graph replay, cuBLAS beside it), the fixed-size sweep
+(S/D/C/Z, m = 1..16, N = 1e3/1e5/1e6,
 op N/N, alpha = 1.5, beta in {0, -0.5}), the op sweep (complex single, all 9
 op pairs at N = 1e5), FEM-like rectangular shapes (S/D, N = 5e5, op(A) = T,
 beta = 1), the interface comparison (3-D layout vs pointer arrays vs cuBLAS,
@@ -218,6 +220,62 @@ def time_cublas(pools, dtype, m, n, k, N, reps):
     return robust_mean(ts[1:])
 
 
+def small_case(pools, reps=41, m=10, N=10_000):
+    """The small configuration: fp32, m = n = k = 10, N = 1e4, op N/N, alpha = 1,
+    beta = 0 (12 MB, L2-resident, launch-bound: no roofline fraction).  Per
+    call, cold (L2 evicted before each call) and hot (calls back to back),
+    issued directly and replayed from a CUDA graph, with cuBLAS strided
+    batched beside it: p10 / p50 / p90 and the robust mean of `reps` timed
+    calls, in microseconds."""
+    torch = pools.torch
+    S = m * m
+    s = torch.cuda.Stream(device=pools.A.device)
+    call = sbgemm.prepare_uniform("s", "N", "N", m, m, m, 1.0, pools.A, m, S, pools.B, m, S, 0.0,
+                                  pools.C, m, S, N, stream=s)
+    A = pools.A[:N * S].view(N, m, m)
+    B = pools.B[:N * S].view(N, m, m)
+    C = pools.C[:N * S].view(N, m, m)
+    ours = lambda: call()
+    cublas = lambda: torch.bmm(B, A, out=C)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        call()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        call()
+    replay = lambda: g.replay()
+
+    def per_call(fn, cold):
+        ts = []
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                fn()
+            for _ in range(reps):
+                if cold:
+                    pools.evict()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                fn()
+                e1.record(s)
+                ts.append((e0, e1))
+        torch.cuda.synchronize()
+        us = sorted(a.elapsed_time(b) * 1e3 for a, b in ts)
+        q = lambda f: us[min(len(us) - 1, int(f * len(us)))]
+        return {"p10_us": round(q(0.1), 2), "p50_us": round(q(0.5), 2), "p90_us": round(q(0.9), 2),
+                "mean_us": round(robust_mean([u * 1e-3 for u in us]) * 1e3, 2)}
+
+    flops = 2 * m * m * m * N
+    rows = []
+    for name, fn in (("direct", ours), ("graph_replay", replay), ("cublas", cublas)):
+        for cold in (True, False):
+            r = {"dtype": "s", "op": "NN", "m": m, "n": m, "k": m, "N": N, "beta": "0.0",
+                 "path": name, "l2": "cold" if cold else "hot"}
+            r.update(per_call(fn, cold))
+            r["gflops_p50"] = round(flops / (r["p50_us"] * 1e-6) / 1e9, 1)
+            rows.append(r)
+    return rows
+
+
 def size_class(N):
     c = 0
     while N >= 10 and c < 7:
@@ -244,7 +302,7 @@ def main(argv=None):
     ap.add_argument("--out", default="sweep.json")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
-    ap.add_argument("--sections", default="fixed,ops,fem,interface,shared_a,16bit",
+    ap.add_argument("--sections", default="small,fixed,ops,fem,interface,shared_a,16bit",
                     help="comma-separated subset of the sections to run "
                          "(grouped_config and once run only when named)")
     args = ap.parse_args(argv)
@@ -288,6 +346,10 @@ def main(argv=None):
         rows.append(r)
         print(json.dumps(r), flush=True)
 
+    # the small configuration (L2-resident, launch-bound)
+    if "small" in want:
+        for r in small_case(pools):
+            emit(r, "small")
     # fixed-size sweep, op N/N
     if "fixed" in want:
         for dtype in ("s", "d", "c", "z"):
