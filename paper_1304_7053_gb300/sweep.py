@@ -23,7 +23,9 @@ N = 1e5), one A shared by all pairs (lda2 = 0, N = 1e6; algorithmic bytes
 count B and C only), and 16-bit storage (binary16/bfloat16, m in
 {8, 12, 16}, N = 1e6).  ``grouped_config`` (only when named) sweeps the
 launch configuration of the grouped call on the fp32 and fp64 sizes 1..16
-workload; ``once`` (only when named) makes one untimed call per type and
+workload; ``vbatch`` (only when named) compares the variable-size plan with
+cublasSgemmGroupedBatched on the fp32 mixed-size batch; ``once`` (only when
+named) makes one untimed call per type and
 size (fp32 and fp64, m = 8..16, N = 1e5, op N/N, alpha = 1, beta = 0, L2
 evicted before each): the launches a kernel-level profile reads.
 """
@@ -276,6 +278,125 @@ def small_case(pools, reps=41, m=10, N=10_000):
     return rows
 
 
+def _cublas():
+    """cuBLAS handle functions and cublasSgemmGroupedBatched through ctypes
+    (the comparator only; nothing of this library calls cuBLAS)."""
+    import ctypes.util
+    for name in ("libcublas.so.13", "libcublas.so"):
+        try:
+            lib = ctypes.CDLL(name)
+            break
+        except OSError:
+            lib = None
+    if lib is None or not hasattr(lib, "cublasSgemmGroupedBatched"):
+        return None
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    lib.cublasCreate_v2.argtypes = [ctypes.POINTER(vp)]
+    lib.cublasSetStream_v2.argtypes = [vp, vp]
+    lib.cublasDestroy_v2.argtypes = [vp]
+    lib.cublasSgemmGroupedBatched.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                              vp, i, vp]
+    for f in ("cublasCreate_v2", "cublasSetStream_v2", "cublasDestroy_v2",
+              "cublasSgemmGroupedBatched"):
+        getattr(lib, f).restype = i
+    return lib
+
+
+def vbatch_compare(dev, N=1_000_000, reps=20):
+    """The variable-size batch (fp32, N problems, m = n = k = p + 1 with
+    P(p) ~ 1/p, beta per problem in {0, 1}, back to back in one arena): this
+    library's plan (one persistent launch) against cublasSgemmGroupedBatched
+    on the same arena (problems grouped by size and beta, device arrays of
+    pointers).  Both start from the same C once and their results are
+    compared; then `reps` runs of each back to back (0.65 GB per run)."""
+    import torch
+    from . import inputs
+    lib = _cublas()
+    desc, la, lb, lc = inputs.vbatch_problems(N, seed=0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    A = torch.rand(la, device=dev, generator=gen) * 2 - 1
+    B = torch.rand(lb, device=dev, generator=gen) * 2 - 1
+    C0 = torch.rand(lc, device=dev, generator=gen) * 2 - 1
+    sizes = desc[:, 0]
+    bz = (desc[:, 3] >> 4) & 1
+    alg_bytes = int(np.sum(4 * sizes * sizes * (3 + (1 - bz))))
+    flops = int(np.sum(2 * sizes ** 3))
+    s = torch.cuda.Stream(device=dev)
+    plan = sbgemm.VPlan("s", sbgemm.vproblems_from_desc(desc))
+    C1 = C0.clone()
+    out = {"problems": N, "algorithmic_bytes": alg_bytes}
+
+    def timed(fn):
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return {"ms": round(ms, 4), "gbps": round(alg_bytes / (ms * 1e-3) / 1e9, 1),
+                "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+
+    with torch.cuda.stream(s):
+        plan.run(1.0, A, B, 1.0, C1, stream=s)
+    torch.cuda.synchronize()
+    if lib is None:
+        out["sbgemm_vbatch"] = timed(lambda: plan.run(1.0, A, B, 1.0, C1, stream=s))
+        plan.close()
+        out["cublas_grouped"] = "unavailable: cublasSgemmGroupedBatched not found"
+        return out
+    # groups: (size, beta-zero); problems of a group in arena order
+    keys = sizes * 2 + bz
+    order = np.argsort(keys, kind="stable")
+    gk, gsize = np.unique(keys[order], return_counts=True)
+    G = len(gk)
+    gm = (gk // 2).astype(np.int32)
+    gbeta = np.where(gk % 2 == 1, 0.0, 1.0).astype(np.float32)
+    ops = np.zeros(G, dtype=np.int32)                       # CUBLAS_OP_N
+    alpha = np.ones(G, dtype=np.float32)
+    gsize = gsize.astype(np.int32)
+    C2 = C0.clone()
+    offs = desc[order]
+    ptrs = np.stack([A.data_ptr() + 4 * offs[:, 4], B.data_ptr() + 4 * offs[:, 5],
+                     C2.data_ptr() + 4 * offs[:, 6]]).astype(np.int64)
+    dptr = torch.from_numpy(ptrs).to(dev)
+    h = ctypes.c_void_p()
+    if lib.cublasCreate_v2(ctypes.byref(h)) != 0:
+        out["sbgemm_vbatch"] = timed(lambda: plan.run(1.0, A, B, 1.0, C1, stream=s))
+        plan.close()
+        out["cublas_grouped"] = "unavailable: cublasCreate failed"
+        return out
+    lib.cublasSetStream_v2(h, ctypes.c_void_p(s.cuda_stream))
+    ad = lambda x: ctypes.c_void_p(x.ctypes.data)
+    keep = (ops, gm, alpha, gbeta, gsize)
+
+    def cub():
+        st = lib.cublasSgemmGroupedBatched(
+            h, ad(ops), ad(ops), ad(gm), ad(gm), ad(gm), ad(alpha),
+            ctypes.c_void_p(dptr[0].data_ptr()), ad(gm), ctypes.c_void_p(dptr[1].data_ptr()),
+            ad(gm), ad(gbeta), ctypes.c_void_p(dptr[2].data_ptr()), ad(gm), G, ad(gsize))
+        if st != 0:
+            raise RuntimeError(f"cublasSgemmGroupedBatched status {st}")
+    try:
+        with torch.cuda.stream(s):
+            cub()
+        torch.cuda.synchronize()
+        # one run of each from the same C: the same products up to rounding
+        out["max_abs_diff_first_run"] = (C1 - C2).abs().max().item()
+        out["sbgemm_vbatch"] = timed(lambda: plan.run(1.0, A, B, 1.0, C1, stream=s))
+        out["cublas_grouped"] = timed(cub)
+        out["cublas_groups"] = G
+    finally:
+        lib.cublasDestroy_v2(h)
+        plan.close()
+        del keep
+    return out
+
+
 def size_class(N):
     c = 0
     while N >= 10 and c < 7:
@@ -304,7 +425,7 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
     ap.add_argument("--sections", default="small,fixed,ops,fem,interface,shared_a,16bit",
                     help="comma-separated subset of the sections to run "
-                         "(grouped_config and once run only when named)")
+                         "(grouped_config, vbatch and once run only when named)")
     args = ap.parse_args(argv)
     want = set(args.sections.split(","))
     import torch
@@ -335,6 +456,16 @@ def main(argv=None):
                                           100_000)
         torch.cuda.synchronize()
         want.discard("once")
+        if not want:
+            with open(args.out, "w") as f:
+                json.dump(rows, f)
+            return rows
+    if "vbatch" in want:
+        r = vbatch_compare(dev)
+        r["section"] = "vbatch"
+        rows.append(r)
+        print(json.dumps(r), flush=True)
+        want.discard("vbatch")
         if not want:
             with open(args.out, "w") as f:
                 json.dump(rows, f)
