@@ -3,7 +3,8 @@
 Workload (the paper's basic parameter set, Section 7): for every square size
 m = 1..16, one batch of N = 100,000 independent pairs, fp32, op = N/N,
 alpha = 1, beta = 0, minimal leading dimensions.  One step runs the 16
-batches through the C ABI (16 kernel launches).  Inputs are seeded
+batches through the C ABI as one grouped call (one persistent launch); the
+same step as 16 uniform calls is reported beside it.  Inputs are seeded
 synthetic uniform[-1, 1] data resident in HBM.  The step touches 1.8 GB, far
 more than the 129 MB L2, so every batch starts cold without an explicit
 flush.
@@ -544,8 +545,18 @@ def oracle_sample(budget_s, threads):
         secs += dt
         flops += flops_per_pair(m) * n
         counts[m] = n
+    # when the whole workload takes less than the budget, repeat it so the
+    # timing covers about the budget (a steadier figure than one short pass)
+    passes = 1
+    if all(counts[m] == N_PAIRS for m in SIZES) and 0.0 < secs < budget_s:
+        one = secs
+        for _ in range(min(20, int(budget_s / one) - 1)):
+            for m in SIZES:
+                secs += run(m, N_PAIRS)
+                flops += flops_per_pair(m) * N_PAIRS
+            passes += 1
     desc = ("oracle (double-double triple loop), fp32 NN alpha=1 beta=0, sizes 1-16, pairs per "
-            "size " + ",".join(f"{m}:{counts[m]}" for m in SIZES))
+            "size " + ",".join(f"{m}:{counts[m]}" for m in SIZES) + f", {passes} pass(es)")
     return flops / secs / 1e9, desc, threads, secs
 
 
