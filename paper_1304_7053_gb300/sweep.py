@@ -34,7 +34,6 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
-import math
 import sys
 
 import numpy as np
@@ -281,7 +280,6 @@ def small_case(pools, reps=41, m=10, N=10_000):
 def _cublas():
     """cuBLAS handle functions and cublasSgemmGroupedBatched through ctypes
     (the comparator only; nothing of this library calls cuBLAS)."""
-    import ctypes.util
     for name in ("libcublas.so.13", "libcublas.so"):
         try:
             lib = ctypes.CDLL(name)
