@@ -324,6 +324,27 @@ def test_full_size_sampled(m):
     H.assert_parity(sub, gsub, ref, 1.0, 0.0)
 
 
+@pytest.mark.parametrize("dtype", ["s", "d"])
+@pytest.mark.parametrize("shape", [(4, 16, 4), (9, 16, 9), (16, 8, 16), (3, 9, 3), (16, 16, 1)])
+def test_fem_shapes_full_size_sampled(dtype, shape):
+    """The FEM-shaped batches at their benchmarked size (N = 500,000,
+    op(A) = T, op(B) = N, alpha = 1, beta = 1) in the default launch
+    configuration, checked on a sample of pairs (and the last pair) that the
+    oracle computes one by one."""
+    m, n, k = shape
+    N = 500_000
+    b = inputs.UniformBatch(dtype, "T", "N", m, n, k, N, seed=73)
+    got = H.run_gpu(b, 1.0, 1.0)
+    pick = np.unique((inputs.splitmix64(79, 300) % np.uint64(N)).astype(np.int64))
+    pick = np.concatenate([pick, [N - 1]])
+    sub = inputs.UniformBatch(dtype, "T", "N", m, n, k, pick.size, seed=0)
+    sub.A = b.A.reshape(N, k * m)[pick].ravel().copy()
+    sub.B = b.B.reshape(N, k * n)[pick].ravel().copy()
+    sub.C = b.C.reshape(N, m * n)[pick].ravel().copy()
+    H.assert_parity(sub, got.reshape(N, m * n)[pick].ravel().copy(), H.oracle_ref(sub, 1.0, 1.0),
+                    1.0, 1.0)
+
+
 def test_million_pairs_size16_sampled():
     N, m = 1_000_000, 16
     b = inputs.UniformBatch("s", "T", "N", m, m, m, N, seed=67)
