@@ -38,3 +38,23 @@ def test_traffic_record_is_tied_to_kernel_sources():
     # the recorded DRAM bytes are returned only for the sources they were taken with
     assert got == (rec[key]["dram_bytes_per_launch"] if rec[key]["source_hash"] == h else None)
     assert bench.ncu_traffic("no such kernel") is None
+
+
+def test_measurement_arithmetic():
+    """The numerators of every reported rate: flops 2mnk (real) or 8mnk
+    (complex) per pair (Section 7), algorithmic bytes s*(mk + kn + mn*(1 +
+    [beta != 0])) per pair; the bench's step is 3.70 GFLOP and 1.795 GB, and
+    the paper's Table implies 128 GFLOP/s for the same step on its K20c."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1304_7053_gb300 import sweep
+    r = sweep.row("c", "T", "N", 3, 9, 3, 1000, -0.5, 1.0)        # 1 ms
+    assert r["gflops"] == round(8 * 3 * 9 * 3 * 1000 / 1e-3 / 1e9, 1)
+    assert r["gbps"] == round(8 * 1000 * (9 + 27 + 27 * 2) / 1e-3 / 1e9, 1)
+    r = sweep.row("s", "N", "N", 16, 16, 16, 100_000, 0.0, 1.0)
+    assert r["gbps"] == round(4 * 100_000 * 3 * 256 / 1e-3 / 1e9, 1)
+    assert r["gflops"] == round(2 * 4096 * 100_000 / 1e-3 / 1e9, 1)
+    fl = sum(bench.flops_per_pair(m) * bench.N_PAIRS for m in bench.SIZES)
+    by = sum(bench.bytes_per_pair(m) * bench.N_PAIRS for m in bench.SIZES)
+    assert fl == 3_699_200_000 and by == 1_795_200_000
+    assert 127.0 < bench.paper_aggregate_gflops() < 129.0
