@@ -591,6 +591,19 @@ def run_reference(args, rank, world):
             "wall_s": round(time.perf_counter() - t_all, 1)}
 
 
+def relaunch_command(gpus, argv, port=None):
+    """The torch.distributed.run command that starts `gpus` ranks of this
+    script on one node (loopback rendezvous on a free port)."""
+    if port is None:
+        import socket
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={gpus}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+            os.path.abspath(__file__), *argv]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,9 +625,17 @@ def main():
     if args.sizes != "1-16":
         SIZES = [int(x) for x in args.sizes.split(",")]
 
+    if args.gpus < 1:
+        sys.exit("bench.py: --gpus must be at least 1")
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: start one rank per GPU through torch.distributed.run
+        # and report its result (rank 0 prints the JSON line)
+        sys.exit(subprocess.call(relaunch_command(args.gpus, sys.argv[1:])))
     rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but the launcher started {world} ranks")
 
     if args.impl == "reference":
         out = run_reference(args, rank, world)

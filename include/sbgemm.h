@@ -489,6 +489,17 @@ sbgemm_status sbgemm_mlp_adam(long long n, float* params, const float* grads, fl
  */
 sbgemm_status sbgemm_device_error(int* code, void* stream);
 
+/*
+ * Self-test of the failure detection above (no counterpart in the paper):
+ * one thread arms a barrier for copies that are never issued and waits on
+ * it with the same bounded wait the kernels use, giving up after
+ * `spin_limit` polls (1 .. 4194304, else SBGEMM_ERR_INVALID_VALUE).  The
+ * expired wait records SBGEMM_ERR_TIMEOUT in the device error word, which
+ * the next sbgemm_device_error reports and clears; the kernel then returns
+ * with nothing in flight, so the context stays usable.  Queued on `stream`.
+ */
+sbgemm_status sbgemm_wait_selftest(long long spin_limit, void* stream);
+
 const char* sbgemm_status_string(sbgemm_status status);
 
 /* Library version as major*10000 + minor*100 + patch. */

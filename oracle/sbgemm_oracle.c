@@ -23,7 +23,7 @@
  * is tested to.  The result is returned unrounded as a (hi, lo) pair of
  * doubles per real component.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - beta == 0 means C is never read (the a1b0 functor of Section 5 never
  *     reads y); NaN or Inf in C then cannot reach the result.
  *   - alpha == 0 or k == 0 gives C = beta*C and A, B are not read.

@@ -6,6 +6,7 @@
 // and beta when they are host scalars (the functor choice of Section 5:
 // beta == 0 never reads C; alpha == 0 or k == 0 reduces to C = beta*C),
 // picks a kernel variant from the selection table, and launches.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -19,15 +20,15 @@
 namespace sbg {
 
 int num_sms() {
-    static int cache[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (cache[dev] == 0) {
-        int v = 0;
+    static std::atomic<int> cache[kMaxDevices];
+    const int dev = current_device();
+    if (dev < 0) return 1;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
-        cache[dev] = v;
+        cache[dev].store(v, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return v;
 }
 
 // Error word written by kernels whose bounded waits expire (one per
@@ -35,15 +36,30 @@ int num_sms() {
 __device__ int g_device_error;
 
 int* device_error_ptr() {
-    static int* cache[64] = {nullptr};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!cache[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
-        cache[dev] = static_cast<int*>(p);
+    static std::atomic<int*> cache[kMaxDevices];
+    const int dev = current_device();
+    if (dev < 0) return nullptr;
+    int* p = cache[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_device_error) != cudaSuccess) return nullptr;
+        p = static_cast<int*>(a);
+        cache[dev].store(p, std::memory_order_release);
     }
-    return cache[dev];
+    return p;
+}
+
+// Failure-detection self-test: thread 0 arms a barrier for 16 bytes of
+// copies that are never issued and waits on it with the kernels' bounded
+// wait (at most `limit` polls); the expired wait is recorded like any other.
+// No copy is in flight when the kernel returns.
+__global__ void wait_selftest_kernel(long long limit, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!mbar_wait(&bar, 0, limit) && err) atomicExch(err, (int)SBGEMM_ERR_TIMEOUT);
 }
 
 namespace {
@@ -405,6 +421,14 @@ sbgemm_status sbgemm_device_error(int* code, void* stream) {
     if (e != cudaSuccess) return (sbgemm_status)e;
     *code = v;
     return SBGEMM_SUCCESS;
+}
+
+sbgemm_status sbgemm_wait_selftest(long long spin_limit, void* stream) {
+    if (spin_limit < 1 || spin_limit > sbg::kSpinLimit) return SBGEMM_ERR_INVALID_VALUE;
+    int* err = sbg::device_error_ptr();
+    if (!err) return SBGEMM_ERR_NOT_SUPPORTED;
+    sbg::wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(spin_limit, err);
+    return (sbgemm_status)cudaGetLastError();
 }
 
 int sbgemm_version(void) { return 100; }

@@ -280,23 +280,14 @@ sbgemm_status grouped_launch_nt(const GIn* in, int n, const void* alpha, const v
     }
     auto kern = grouped_kernel<Ty, NT>;
     const size_t smem = gsmem_bytes(cfg);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        attr = true;
-    }
-    // occupancy, cached per shared-memory size and device
-    static thread_local size_t occ_smem = ~(size_t)0;
-    static thread_local int occ_dev = -1, occ_val = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (occ_smem != smem || occ_dev != dev) {
-        int v = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, NT, smem);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        occ_smem = smem; occ_dev = dev; occ_val = v;
-    }
+    // per instantiation and device
+    static DeviceFlags attr;
+    static thread_local OccCache occ;
+    cudaError_t ae = ensure_smem_limit(kern, 220 * 1024, attr);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
+    int occ_val = 0;
+    ae = blocks_per_sm(kern, NT, smem, occ, &occ_val);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
     if (occ_val < 1) return SBGEMM_ERR_NOT_SUPPORTED;
     long long grid = (long long)num_sms() * occ_val;
     if (grid > g.total_tiles) grid = g.total_tiles;

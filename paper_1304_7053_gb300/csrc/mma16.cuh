@@ -306,22 +306,14 @@ sbgemm_status launch_mma16(const Req& r) {
     g.P = P;
     const size_t smem = (size_t)g.stages * P * per_pair;
     auto kern = mma16_kernel<Ty, M>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        attr = true;
-    }
-    static thread_local size_t occ_smem = ~(size_t)0;
-    static thread_local int occ_dev = -1, occ_val = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (occ_smem != smem || occ_dev != dev) {
-        int v = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 128, smem);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        occ_smem = smem; occ_dev = dev; occ_val = v;
-    }
+    // per instantiation and device
+    static DeviceFlags attr;
+    static thread_local OccCache occ;
+    cudaError_t ae = ensure_smem_limit(kern, 220 * 1024, attr);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
+    int occ_val = 0;
+    ae = blocks_per_sm(kern, 128, smem, occ, &occ_val);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
     if (occ_val < 1) return SBGEMM_ERR_NOT_SUPPORTED;
     const long long ntiles = (r.batch + P - 1) / P;
     long long grid = (long long)num_sms() * occ_val;

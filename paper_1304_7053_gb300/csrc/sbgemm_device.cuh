@@ -163,10 +163,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                  :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// wait for the phase with the given parity to complete; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// wait for the phase with the given parity to complete; false when `limit`
+// polls have not seen it
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = kSpinLimit) {
     const unsigned a = smem_u32(bar);
-    for (long long i = 0; i < kSpinLimit; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"

@@ -1,6 +1,7 @@
 // Kernels and host-side launchers for the fixed-size uniform-layout path.
 #pragma once
 
+#include "device_setup.h"
 #include "sbgemm_device.cuh"
 #include "tile_table.h"
 #include "../../include/sbgemm.h"
@@ -419,27 +420,14 @@ sbgemm_status launch_pipe_k(const Req& r, const LaunchOpts& o) {
     a.P = gm.P;
     a.stages = o.stages;
     auto kern = pipe_kernel<Cf, PF>;
-    static bool attr_set = false;   // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        attr_set = true;
-    }
-    // occupancy per dynamic shared-memory size, cached per instantiation
-    // (the query costs microseconds of host time on every call otherwise)
-    static thread_local size_t occ_smem = ~(size_t)0;
-    static thread_local int occ_val = 0;
-    static thread_local int occ_dev = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
+    // per instantiation and device
+    static DeviceFlags attr_set;
+    static thread_local OccCache occ;
+    cudaError_t ae = ensure_smem_limit(kern, 220 * 1024, attr_set);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
     int per_sm = 0;
-    if (occ_smem == gm.smem && occ_dev == dev) {
-        per_sm = occ_val;
-    } else {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cf::NT, gm.smem);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        occ_smem = gm.smem; occ_val = per_sm; occ_dev = dev;
-    }
+    ae = blocks_per_sm(kern, Cf::NT, gm.smem, occ, &per_sm);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
     if (per_sm < 1) return SBGEMM_ERR_NOT_SUPPORTED;
     if (o.ctas_per_sm > 0 && per_sm > o.ctas_per_sm) per_sm = o.ctas_per_sm;
     const long long ntiles = ((long long)r.batch + gm.P - 1) / gm.P;

@@ -495,20 +495,15 @@ sbgemm_status vbatch_launch(const VItem* items, int n_items, const VRec* recs, i
     }
     g.max_tile = kVMaxTile;
     const size_t smem = vbatch_smem_bytes(Ty::code);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(vbatch_kernel<Ty>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        attr = true;
-    }
-    static thread_local int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatch_kernel<Ty>,
-                                                                      kVThreads, smem);
-        if (e != cudaSuccess) return (sbgemm_status)e;
-        if (per_sm < 1) return SBGEMM_ERR_NOT_SUPPORTED;
-    }
+    // per instantiation and device
+    static DeviceFlags attr;
+    static thread_local OccCache occ;
+    cudaError_t ae = ensure_smem_limit(vbatch_kernel<Ty>, (int)smem, attr);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
+    int per_sm = 0;
+    ae = blocks_per_sm(vbatch_kernel<Ty>, kVThreads, smem, occ, &per_sm);
+    if (ae != cudaSuccess) return (sbgemm_status)ae;
+    if (per_sm < 1) return SBGEMM_ERR_NOT_SUPPORTED;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return (sbgemm_status)e;
     long long grid = (long long)num_sms() * per_sm;

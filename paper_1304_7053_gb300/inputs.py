@@ -39,9 +39,10 @@ def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
     return z
 
 
-def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
-    """``count`` float64 draws, uniform on [lo, hi), from 53-bit mantissas."""
-    u = (splitmix64(seed, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0, start: int = 0) -> np.ndarray:
+    """Draws start .. start+count-1 as float64, uniform on [lo, hi), from
+    53-bit mantissas."""
+    u = (splitmix64(seed, count, start) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
     return lo + (hi - lo) * u
 
 
@@ -83,6 +84,73 @@ def draw(dtype: str, count: int, seed: int, int_valued: bool = False) -> np.ndar
     n = count * (2 if dtype in ("c", "z") else 1)
     x = small_ints(seed, n) if int_valued else uniform(seed, n)
     return to_storage(x, dtype)
+
+
+# ---------------------------------------------------------------- large batches
+#
+# Batches of 1e5-1e6 pairs are drawn on the device (torch elementwise ops)
+# from the same counter-based streams, so a full-size case costs no host
+# generation or transfer; the host functions below give any element range of
+# the same stream, and the tests check that the two agree on the pairs they
+# sample.  Draws: uniform[-1, 1) exactly as ``uniform`` (float64, rounded to
+# the storage type) for s, d, c, z and bfloat16; for binary16 a grid of
+# 2^-10 steps on [-1, 1), exact in the format, so no conversion rounding is
+# involved on either side.
+
+GRID16_BITS = 11          # binary16 grid: k * 2^-10, k uniform in [-1024, 1024)
+
+
+def draw_range(dtype: str, seed: int, start: int, count: int) -> np.ndarray:
+    """Elements start .. start+count-1 of the large-batch stream ``seed`` of
+    storage type ``dtype`` (host side of ``device_draw``)."""
+    w = 2 if dtype in ("c", "z") else 1
+    if dtype == "h":
+        z = splitmix64(seed, count, start)
+        k = (z >> np.uint64(64 - GRID16_BITS)).astype(np.int64) - (1 << (GRID16_BITS - 1))
+        return (k.astype(np.float64) * 2.0 ** -(GRID16_BITS - 1)).astype(np.float16).view(np.uint16)
+    return to_storage(uniform(seed, count * w, start=start * w), dtype)
+
+
+def device_draw(dtype: str, count: int, seed: int, device, chunk: int = 1 << 26):
+    """``count`` elements of the large-batch stream ``seed`` as a flat torch
+    tensor on ``device`` (complex types as float pairs, 16-bit types as
+    int16 bit patterns); element e equals ``draw_range(dtype, seed, e, 1)``."""
+    import torch
+
+    w = 2 if dtype in ("c", "z") else 1
+    n = count * w
+    real = {"s": torch.float32, "c": torch.float32, "d": torch.float64, "z": torch.float64,
+            "b": torch.bfloat16, "h": torch.float16}[dtype]
+    out = torch.empty(n, dtype=real, device=device)
+
+    def as_i64(v):
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    gold, m1, m2 = as_i64(int(_GOLDEN)), as_i64(int(_M1)), as_i64(int(_M2))
+    s64 = as_i64(seed & 0xFFFFFFFFFFFFFFFF)
+
+    def lsr(z, r):           # logical shift right of int64 bit patterns
+        return (z >> r) & ((1 << (64 - r)) - 1)
+
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        # int64 arithmetic wraps modulo 2^64: the uint64 recurrence bit for bit
+        z = torch.arange(c0 + 1, c1 + 1, dtype=torch.int64, device=device) * gold + s64
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        if dtype == "h":
+            k = lsr(z, 64 - GRID16_BITS) - (1 << (GRID16_BITS - 1))
+            out[c0:c1] = (k.to(torch.float64) * 2.0 ** -(GRID16_BITS - 1)).to(torch.float16)
+        else:
+            u = lsr(z, 11).to(torch.float64) * (2.0 ** -53)
+            x = -1.0 + 2.0 * u
+            if dtype == "b":
+                x = x.to(torch.float32)
+            out[c0:c1] = x.to(real)
+    if dtype in ("h", "b"):
+        return out.view(torch.int16)
+    return out
 
 
 def stored_shape(op: str, rows: int, cols: int):

@@ -44,6 +44,7 @@ SIGNATURES = {
     "sbgemm_grouped_config": (_i, [_i, _i, _i, _i]),
     "sbgemm_vbatch_config": (_i, [_i]),
     "sbgemm_device_error": (_i, [_vp, _vp]),
+    "sbgemm_wait_selftest": (_i, [_ll, _vp]),
     "sbgemm_Sgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),
     "sbgemm_Dgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),
     "sbgemm_Cgemm_multi_nounif": (_i, [_c, _c, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, _i, _i]),

@@ -11,7 +11,7 @@ library's kernels).  The comparator is
 cuBLAS strided-batched GEMM through torch.bmm on the same column-major data
 (C = A B column-major is C^T = B^T A^T row-major).
 
-    python -m paper_1304_7053_gb300.sweep --out sweep.json [--quick]
+    python sweep.py --out sweep.json [--quick]
 
 Sections: the small configuration (fp32, m = 10, N = 1e4: cold and hot,
 direct and CUDA-graph replay, cuBLAS beside it), the fixed-size sweep
@@ -34,11 +34,16 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
+import os
 import sys
 
 import numpy as np
 
-from . import sbgemm
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1304_7053_gb300 import sbgemm  # noqa: E402
 
 ES = {"s": 4, "d": 8, "c": 8, "z": 16, "h": 2, "b": 2}
 CPLX = {"c", "z"}
@@ -308,7 +313,7 @@ def vbatch_compare(dev, N=1_000_000, reps=20):
     pointers).  Both start from the same C once and their results are
     compared; then `reps` runs of each back to back (0.65 GB per run)."""
     import torch
-    from . import inputs
+    from paper_1304_7053_gb300 import inputs
     lib = _cublas()
     desc, la, lb, lc = inputs.vbatch_problems(N, seed=0)
     gen = torch.Generator(device=dev)

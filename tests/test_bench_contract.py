@@ -47,7 +47,7 @@ def test_measurement_arithmetic():
     the paper's Table implies 128 GFLOP/s for the same step on its K20c."""
     sys.path.insert(0, ROOT)
     import bench
-    from paper_1304_7053_gb300 import sweep
+    import sweep
     r = sweep.row("c", "T", "N", 3, 9, 3, 1000, -0.5, 1.0)        # 1 ms
     assert r["gflops"] == round(8 * 3 * 9 * 3 * 1000 / 1e-3 / 1e9, 1)
     assert r["gbps"] == round(8 * 1000 * (9 + 27 + 27 * 2) / 1e-3 / 1e9, 1)
@@ -58,3 +58,26 @@ def test_measurement_arithmetic():
     by = sum(bench.bytes_per_pair(m) * bench.N_PAIRS for m in bench.SIZES)
     assert fl == 3_699_200_000 and by == 1_795_200_000
     assert 127.0 < bench.paper_aggregate_gflops() < 129.0
+
+
+def test_gpus_without_launcher_starts_one_rank_per_gpu():
+    """`bench.py --gpus 2` with no launcher in the environment starts two
+    ranks itself (never a silent one-rank run); shown on the reference arm,
+    which runs on the host cores."""
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--impl", "reference",
+                        "--steps", "1", "--warmup", "3", "--ref-budget", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    assert json.loads(lines[0])["n_gpus"] == 2
+
+
+def test_gpus_disagreeing_with_launcher_is_an_error():
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--impl", "reference",
+                        "--steps", "1", "--warmup", "3", "--ref-budget", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode != 0 and "launcher started 1 ranks" in r.stderr

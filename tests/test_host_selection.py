@@ -5,7 +5,8 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
-from paper_1304_7053_gb300 import selector, sweep
+import sweep
+from paper_1304_7053_gb300 import selector
 
 
 def test_robust_mean_resolves_below_a_timer_step():

@@ -457,6 +457,54 @@ def test_vbatch_matches_numpy_per_problem():
         np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("dtype", ["s", "d", "c", "z", "h", "b"])
+def test_vbatch_every_storage_type_matches_numpy(dtype):
+    """The per-type element size and decode of the variable-size oracle:
+    problems at nonzero, unequal offsets in the three arenas (the arenas
+    have different lengths, so a wrong element size moves every later
+    problem's operands), mixed ops and beta, against numpy problem by
+    problem on the decoded inputs."""
+    rng = inputs.splitmix64(901, 64)
+    count = 60
+    shapes = [(1 + int(r % np.uint64(16)), 1 + int((r >> np.uint64(8)) % np.uint64(16)),
+               1 + int((r >> np.uint64(16)) % np.uint64(16))) for r in rng[:count]]
+    desc = np.zeros((count, 8), dtype=np.int64)
+    oa = ob = oc = 0
+    for q, (m, n, k) in enumerate(shapes):
+        fl = int(rng[q] >> np.uint64(24)) % 3 | ((int(rng[q] >> np.uint64(28)) % 3) << 2)
+        fl |= (q % 3 == 0) << 4
+        desc[q] = (m, n, k, fl, oa + 1, ob + 2, oc + 3, 0)
+        oa, ob, oc = oa + m * k + 5, ob + k * n + 7, oc + m * n + 3
+    A = inputs.draw(dtype, oa + 8, 1)
+    B = inputs.draw(dtype, ob + 8, 2)
+    C = inputs.draw(dtype, oc + 8, 3)
+    alpha, beta = ((1.5 - 0.5j, -0.5 + 0.25j) if dtype in "cz" else (1.5, -0.5))
+    out = oracle.gemm_vbatch(dtype, desc, alpha, A, B, beta, C)
+    dec = (lambda x: oracle._decode16(x, dtype)) if dtype in "hb" else (lambda x: x)
+    Ad, Bd, Cd = dec(A), dec(B), dec(C)
+    ref_t = "z" if dtype in "cz" else "d"
+    covered = np.zeros(C.size, dtype=bool)
+    for q in range(count):
+        m, n, k, fl, pa, pb, pc, _ = (int(v) for v in desc[q])
+        ta, tb = "NTC"[fl & 3], "NTC"[(fl >> 2) & 3]
+        if dtype not in "cz":
+            ta, tb = ta.replace("C", "T"), tb.replace("C", "T")
+        be = 0.0 if (fl >> 4) & 1 else beta
+        ar, ac = (m, k) if ta == "N" else (k, m)
+        br, bc = (k, n) if tb == "N" else (n, k)
+        Cq = Cd[pc:pc + m * n].astype(np.complex128 if dtype in "cz" else np.float64)
+        if be == 0.0:
+            Cq = np.full_like(Cq, np.nan)          # beta = 0: C is never read
+        want = refmath.numpy_gemm(ref_t, ta, tb, m, n, k, alpha, Ad[pa:], ar, ar * ac, Bd[pb:],
+                                  br, br * bc, be if be != 0.0 else 0.0,
+                                  np.nan_to_num(Cq), m, m * n, 1)[0]
+        got = refmath.views(out[pc:], m, n, m, m * n, 1)[0]
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+        covered[pc:pc + m * n] = True
+    # entries of C no problem owns keep their old (decoded) values
+    np.testing.assert_array_equal(out[~covered], Cd[~covered])
+
+
 def test_vbatch_size_distribution():
     """Sizes p + 1, p in 1..15 with P(p) proportional to 1/p."""
     s = inputs.vbatch_sizes(200000, seed=0)

@@ -25,6 +25,9 @@ MUTANTS = {
     "alpha_imag_sign": ("dd_neg(dd_mul_d(im, alpha[1]))", "dd_mul_d(im, alpha[1])"),
     "reads_c_when_beta_zero": ("const int read_c = !(", "const int read_c = 1 || !("),
     "dropped_dd_term": ("s.lo += t.hi;", ";"),
+    # variable-size arenas addressed with a wrong element size per type
+    "vbatch_es_z": ("(type == OR_Z) ? 16 : 2;", "(type == OR_Z) ? 8 : 2;"),
+    "vbatch_es_16bit": ("(type == OR_Z) ? 16 : 2;", "(type == OR_Z) ? 16 : 4;"),
 }
 
 
