@@ -59,7 +59,8 @@ enum {
     SBGEMM_ERR_INVALID_VALUE = -5,  /* other invalid argument (mode, variant, plan) */
     SBGEMM_ERR_TIMEOUT = -6,        /* a bounded in-kernel wait gave up */
     SBGEMM_ERR_NOT_SUPPORTED = -7,  /* valid request this build cannot serve */
-    SBGEMM_ERR_CAPACITY = -8        /* request exceeds a fixed capacity */
+    SBGEMM_ERR_CAPACITY = -8,       /* request exceeds a fixed capacity */
+    SBGEMM_ERR_IO = -9              /* a file cannot be read or written, or has a bad format */
 };
 
 /* Where alpha and beta live (Section 4: "host or device pointer"). */
@@ -286,21 +287,115 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
     long long ldc2, int batchCount, int scalar_mode, int variant, void* stream);
 
 /*
- * Selection table: the variant the _async entry points use for
- * (type, m, n, k, opA-transposed, opB-transposed, beta == 0, batch-size
- * class).  sbgemm_set_choice installs one entry (variant < 0 removes it);
- * sbgemm_get_choice returns the installed or default variant.  The table is
- * process-wide host state; set it before issuing work, not concurrently with
- * calls that read it.  size_class = floor(log10(batchCount)) clamped to 0..7.
- * Default without an entry: the tensor-core variant (7) for the 16-bit types
- * at m = n = k = 8 and 16; variant 2 for complex64, and for fp32 with
+ * Variant selection (the tunable launch configuration and specialised
+ * kernels of Section 6).  Every fixed-size call (uniform and pointer-array
+ * forms) runs the variant chosen for its class (type, m, n, k,
+ * opA-transposed, opB-transposed, beta == 0, batch-size class), where
+ * size_class = floor(log10(batchCount)) clamped to 0..7 and beta == 0 is
+ * known only for host scalars (device scalars count as beta != 0).  The
+ * choice depends on the selector mode:
+ *   SBGEMM_SELECTOR_DEFAULT: the built-in rule only;
+ *   SBGEMM_SELECTOR_TABLE (initial mode): the selection table's entry for
+ *     the class, else the built-in rule;
+ *   SBGEMM_SELECTOR_MODEL: the table's entry, else the installed cost
+ *     model's choice, else the built-in rule.
+ * Built-in rule: the tensor-core variant (7) for the 16-bit types at
+ * m = n = k = 8 and 16; variant 2 for complex64, and for fp32 with
  * size_class <= 5; variant 0 otherwise.
+ * All of this is process-wide host state: set it before issuing work, not
+ * concurrently with calls that read it.
+ *
+ * Environment, read once before the first selection or selector call:
+ * SBGEMM_TABLE (a table file to load), SBGEMM_COST_MODEL (a cost-model
+ * file to load) and SBGEMM_SELECTOR (default, table or model).  A failure
+ * is not fatal: the affected setting keeps its initial value and
+ * sbgemm_get_selector reports the first error.
  */
+enum { SBGEMM_SELECTOR_DEFAULT = 0, SBGEMM_SELECTOR_TABLE = 1, SBGEMM_SELECTOR_MODEL = 2 };
+
+/* Install one table entry (variant < 0 removes it). */
 sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
                                 int beta_zero, int size_class, int variant);
+/* The variant a call of this class would run under the current mode
+ * (-1 for an invalid class). */
 int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb,
                       int beta_zero, int size_class);
+/* The built-in rule's variant for the class (-1 for an invalid class). */
+int sbgemm_default_variant(int type, int m, int n, int k, int size_class);
 void sbgemm_clear_choices(void);
+/* The public variant index the calling thread's most recent fixed-size
+ * call ran (-1 before any); for checking which kernel a selection reached. */
+int sbgemm_last_variant(void);
+
+/*
+ * Table files (text): a line "sbgemm-table 1", a line "device <name>"
+ * (the GPU the table was measured on, informational), then one line per
+ * entry "type m n k ta tb beta_zero size_class variant"; '#' starts a
+ * comment line.  Saving writes the whole table (through a temporary file
+ * renamed into place).  Loading validates every line first and then adds
+ * the entries to the table (an entry for a class already present replaces
+ * it); on any error nothing is added.  SBGEMM_ERR_IO for an unreadable,
+ * unwritable or malformed file.
+ */
+sbgemm_status sbgemm_save_table(const char* path);
+sbgemm_status sbgemm_load_table(const char* path);
+
+/* Selector mode (SBGEMM_SELECTOR_*).  MODEL needs an installed cost model
+ * (else SBGEMM_ERR_INVALID_VALUE) and evaluates it first if needed (see
+ * sbgemm_set_cost_model); the mode is unchanged on any error. */
+sbgemm_status sbgemm_set_selector(int mode);
+/* Current mode, and the first error met while applying the environment
+ * settings (0 when none; env_status may be NULL). */
+sbgemm_status sbgemm_get_selector(int* mode, int* env_status);
+
+/*
+ * Cost model of the selector: a network of the sbgemm_mlp_* layout with
+ * F = 16 inputs (the class features: m, n, k / 16; (log10 N - 4.5) / 1.5
+ * at the middle of the size class; the storage-type one-hot in type-code
+ * order; opA and opB transposed; conjugation (0); beta == 0; a flag for
+ * shapes with specialised kernels; (mnk)^(1/3) / 16), H hidden units and
+ * V outputs, output v the standardised log-time of variant v: predicted
+ * time = exp(y_v * log_time_std + log_time_mean).  For each class with more
+ * than one variant the model's choice is the valid variant with the
+ * smallest prediction if that is below (1 - margin) times the prediction
+ * of the built-in rule's variant, else the built-in rule's variant.
+ * sbgemm_set_cost_model copies `params` (host array of
+ * sbgemm_mlp_param_count(F, H, V) floats) and replaces any installed model.
+ * The choices of every class are evaluated at once, on the current GPU,
+ * with sbgemm_mlp_forward (device memory allocated and freed for it, the
+ * call synchronises): right away when the mode is MODEL, else when the
+ * mode becomes MODEL, or at the first call that needs them when the model
+ * and mode come from the environment; make that first call outside any
+ * stream capture.  F must be 16, 1 <= H <= 4096, 1 <= V <= 64,
+ * log_time_std > 0, 0 <= margin < 1 (else SBGEMM_ERR_INVALID_VALUE).
+ */
+sbgemm_status sbgemm_set_cost_model(int F, int H, int V, const float* params,
+                                    double log_time_mean, double log_time_std, double margin);
+/*
+ * Cost-model files (text, version 1): "sbgemm-cost-model 1", "device
+ * <name>" (the GPU it was trained on), "features F hidden H outputs V",
+ * "log_time_mean mu log_time_std sd margin m", "params n", then the n
+ * parameters (9 significant digits, exact for fp32).  Loading installs the
+ * model as sbgemm_set_cost_model does; SBGEMM_ERR_IO for an unreadable or
+ * malformed file; SBGEMM_ERR_INVALID_VALUE from sbgemm_save_cost_model when
+ * no model is installed.
+ */
+sbgemm_status sbgemm_save_cost_model(const char* path);
+sbgemm_status sbgemm_load_cost_model(const char* path);
+
+/*
+ * The autotuner's exhaustive step for one class, natively: times every
+ * variant of the request with sbgemm_time_variant (host scalars; `reps`,
+ * `flush`, `flush_bytes` and `stream` as there), writes the times to ms[v]
+ * when ms is not NULL (sbgemm_num_variants entries), the fastest variant to
+ * *best, and installs it in the selection table for the request's class.
+ * C is overwritten by the timed calls.  Synchronises the stream.
+ */
+sbgemm_status sbgemm_tune(int type, char transa, char transb, int m, int n, int k,
+    const void* alpha, const void* A, int lda, long long lda2,
+    const void* B, int ldb, long long ldb2, const void* beta, void* C, int ldc,
+    long long ldc2, int batchCount, int reps, void* flush, size_t flush_bytes, void* stream,
+    int* best, float* ms);
 
 /* ------------------------------------------------------------------ */
 /* Variable-size batches (Section 1: matrices of different sizes are     */

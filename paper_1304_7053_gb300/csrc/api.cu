@@ -16,6 +16,7 @@
 
 #include "sbgemm_launch.cuh"
 #include "sbgemm_shapes.h"
+#include "selection.h"
 
 namespace sbg {
 
@@ -82,54 +83,6 @@ bool host_scalar_zero(int type, const void* p) {
     case SBGEMM_TYPE_Z: { const double* d = static_cast<const double*>(p); return d[0] == 0.0 && d[1] == 0.0; }
     default: return *static_cast<const float*>(p) == 0.f;
     }
-}
-
-// selection table: (type, m, n, k, ta, tb, beta_zero, size_class) -> variant
-using Key = std::tuple<int, int, int, int, int, int, int, int>;
-std::mutex g_choice_mu;
-std::map<Key, int> g_choice;
-
-int size_class(int batch) {
-    int c = 0;
-    while (batch >= 10 && c < 7) { batch /= 10; ++c; }
-    return c;
-}
-
-int lookup_choice(int type, int m, int n, int k, int ta, int tb, int bz, int sc) {
-    std::lock_guard<std::mutex> lk(g_choice_mu);
-    auto it = g_choice.find(Key(type, m, n, k, ta, tb, bz, sc));
-    return it == g_choice.end() ? -1 : it->second;
-}
-
-// the 16-bit types at m = n = k = 8, 12 or 16 also have the tensor-core variant
-bool has_mma_variant(int type, int m, int n, int k) {
-    return (type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && m == n && n == k &&
-           (m == 8 || m == 12 || m == 16);
-}
-
-int variants_for(int type, int m, int n, int k) {
-    if (m < 1 || n < 1 || k < 1 || m > 16 || n > 16 || k > 16) return 0;
-    if (!has_specialized(0, m, n, k)) return 1;
-    return has_mma_variant(type, m, n, k) ? kMmaVariant + 1 : kNumPipeVariants + 1;
-}
-
-// The variant used when the selection table has no entry (sc: the batch's
-// size class, floor(log10 N)):
-// - the tensor-core kernel for the 16-bit types at m = n = k = 8 and 16
-//   (measured 1.3-1.7x faster; at m = 12 it measured slower than the
-//   CUDA-core kernel with beta = 0 and equal otherwise);
-// - variant 2 (32 KB tiles, two stages: more blocks per SM and a shorter
-//   pipeline to fill) for complex64 and for fp32 below 1e6 pairs: over the
-//   square N/N sizes 2..16 it took 9% less total time than variant 0 for
-//   complex64 at N = 1e5 and 1e6, and 5% less for fp32 at N = 1e5 (up to 20%
-//   per size), while fp32 at N = 1e6 measured the same total;
-// - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
-//   no difference; the 16-bit CUDA-core kernels were mixed).
-int default_variant(int type, int m, int n, int k, int sc) {
-    if (has_mma_variant(type, m, n, k) && m != 12) return kMmaVariant;
-    if (!has_specialized(0, m, n, k)) return 0;
-    if (type == SBGEMM_TYPE_C || (type == SBGEMM_TYPE_S && sc <= 5)) return 2;
-    return 0;
 }
 
 // Map a public variant index to the internal one (generic kernel index =
@@ -212,11 +165,11 @@ sbgemm_status gemm_uniform(int type, char transa, char transb, int m, int n, int
     if (variant >= 0) {
         if (variant >= nv) return SBGEMM_ERR_INVALID_VALUE;
     } else {
-        variant = lookup_choice(type, m, n, k, r.ta, r.tb,
-                                scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
-                                size_class(batch));
-        if (variant < 0 || variant >= nv) variant = default_variant(type, m, n, k, size_class(batch));
+        variant = select_variant(type, m, n, k, r.ta, r.tb,
+                                 scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
+                                 size_class(batch));
     }
+    note_variant(variant);
     r.variant = internal_variant(m, n, k, variant);
     return run_typed(r);
 }
@@ -262,11 +215,10 @@ sbgemm_status gemm_nounif(int type, char transa, char transb, int m, int n, int 
     }
     if (k == 0 || r.alpha_zero) return scale_typed(r);
     if (!Ap || !Bp) return SBGEMM_ERR_NULL_POINTER;
-    int variant = lookup_choice(type, m, n, k, r.ta, r.tb,
-                                scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
-                                size_class(batch));
-    if (variant < 0 || variant >= variants_for(type, m, n, k))
-        variant = default_variant(type, m, n, k, size_class(batch));
+    const int variant = select_variant(type, m, n, k, r.ta, r.tb,
+                                       scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
+                                       size_class(batch));
+    note_variant(variant);
     r.variant = internal_variant(m, n, k, variant);
     return run_typed(r);
 }
@@ -370,28 +322,6 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
                         beta, C, ldc, ldc2, batchCount, scalar_mode, variant, (cudaStream_t)stream);
 }
 
-sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
-                                int beta_zero, int size_class, int variant) {
-    if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B) return SBGEMM_ERR_INVALID_VALUE;
-    const int nv = sbg::variants_for(type, m, n, k);
-    if (nv == 0 || variant >= nv || size_class < 0 || size_class > 7) return SBGEMM_ERR_INVALID_VALUE;
-    std::lock_guard<std::mutex> lk(sbg::g_choice_mu);
-    sbg::Key key(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
-    if (variant < 0) sbg::g_choice.erase(key);
-    else sbg::g_choice[key] = variant;
-    return SBGEMM_SUCCESS;
-}
-
-int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb, int beta_zero, int size_class) {
-    const int v = sbg::lookup_choice(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
-    return v < 0 ? sbg::default_variant(type, m, n, k, size_class) : v;
-}
-
-void sbgemm_clear_choices(void) {
-    std::lock_guard<std::mutex> lk(sbg::g_choice_mu);
-    sbg::g_choice.clear();
-}
-
 const char* sbgemm_status_string(sbgemm_status s) {
     switch (s) {
     case SBGEMM_SUCCESS: return "success";
@@ -403,6 +333,7 @@ const char* sbgemm_status_string(sbgemm_status s) {
     case SBGEMM_ERR_TIMEOUT: return "bounded in-kernel wait expired";
     case SBGEMM_ERR_NOT_SUPPORTED: return "not supported";
     case SBGEMM_ERR_CAPACITY: return "request exceeds a fixed capacity";
+    case SBGEMM_ERR_IO: return "file cannot be read or written, or has a bad format";
     default: return s > 0 ? cudaGetErrorString((cudaError_t)s) : "unknown status";
     }
 }

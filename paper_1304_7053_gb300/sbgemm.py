@@ -22,7 +22,7 @@ SCALARS_HOST, SCALARS_DEVICE = 0, 1
 
 STATUS = {0: "SUCCESS", -1: "ERR_INVALID_TRANS", -2: "ERR_INVALID_SIZE", -3: "ERR_INVALID_LD",
           -4: "ERR_NULL_POINTER", -5: "ERR_INVALID_VALUE", -6: "ERR_TIMEOUT",
-          -7: "ERR_NOT_SUPPORTED", -8: "ERR_CAPACITY"}
+          -7: "ERR_NOT_SUPPORTED", -8: "ERR_CAPACITY", -9: "ERR_IO"}
 
 # Every symbol include/sbgemm.h declares, with its ctypes signature.
 _c, _i, _ll, _vp = ctypes.c_char, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
@@ -57,6 +57,18 @@ SIGNATURES = {
     "sbgemm_set_choice": (_i, [_i] * 9),
     "sbgemm_get_choice": (_i, [_i] * 8),
     "sbgemm_clear_choices": (None, []),
+    "sbgemm_default_variant": (_i, [_i] * 5),
+    "sbgemm_last_variant": (_i, []),
+    "sbgemm_save_table": (_i, [ctypes.c_char_p]),
+    "sbgemm_load_table": (_i, [ctypes.c_char_p]),
+    "sbgemm_set_selector": (_i, [_i]),
+    "sbgemm_get_selector": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "sbgemm_set_cost_model": (_i, [_i, _i, _i, _vp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double]),
+    "sbgemm_save_cost_model": (_i, [ctypes.c_char_p]),
+    "sbgemm_load_cost_model": (_i, [ctypes.c_char_p]),
+    "sbgemm_tune": (_i, [_i] + _UNIFORM + [_i, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i),
+                                           _vp]),
     "sbgemm_vbatch_plan_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _i]),
     "sbgemm_vbatch_plan_destroy": (_i, [_vp]),
     "sbgemm_vbatch_run": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
@@ -256,6 +268,67 @@ def get_choice(dtype, m, n, k, ta, tb, beta_zero, size_class) -> int:
 
 def clear_choices() -> None:
     lib().sbgemm_clear_choices()
+
+
+def default_variant(dtype, m, n, k, size_class) -> int:
+    return lib().sbgemm_default_variant(TYPE_CODES[dtype], m, n, k, size_class)
+
+
+def last_variant() -> int:
+    return lib().sbgemm_last_variant()
+
+
+SELECTOR_DEFAULT, SELECTOR_TABLE, SELECTOR_MODEL = 0, 1, 2
+
+
+def set_selector(mode: int) -> None:
+    st = lib().sbgemm_set_selector(mode)
+    if st != 0:
+        raise SbgemmError(st, "set_selector")
+
+
+def get_selector():
+    """(mode, first error of the environment settings)."""
+    mode, env = ctypes.c_int(), ctypes.c_int()
+    st = lib().sbgemm_get_selector(ctypes.byref(mode), ctypes.byref(env))
+    if st != 0:
+        raise SbgemmError(st, "get_selector")
+    return mode.value, env.value
+
+
+def save_table(path: str) -> None:
+    st = lib().sbgemm_save_table(os.fsencode(path))
+    if st != 0:
+        raise SbgemmError(st, "save_table")
+
+
+def load_table(path: str) -> None:
+    st = lib().sbgemm_load_table(os.fsencode(path))
+    if st != 0:
+        raise SbgemmError(st, "load_table")
+
+
+def set_cost_model(F: int, H: int, V: int, params, log_time_mean: float, log_time_std: float,
+                   margin: float) -> None:
+    """Install a cost model from a host float32 numpy array of parameters."""
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    st = lib().sbgemm_set_cost_model(F, H, V, p.ctypes.data, float(log_time_mean),
+                                     float(log_time_std), float(margin))
+    if st != 0:
+        raise SbgemmError(st, "set_cost_model")
+
+
+def save_cost_model(path: str) -> None:
+    st = lib().sbgemm_save_cost_model(os.fsencode(path))
+    if st != 0:
+        raise SbgemmError(st, "save_cost_model")
+
+
+def load_cost_model(path: str) -> None:
+    st = lib().sbgemm_load_cost_model(os.fsencode(path))
+    if st != 0:
+        raise SbgemmError(st, "load_cost_model")
 
 
 # ---------------------------------------------------------------- variable size

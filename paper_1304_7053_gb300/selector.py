@@ -345,6 +345,24 @@ class CostModel:
         Y, _ = self.forward(X)
         return np.exp(Y.cpu().numpy().astype(np.float64) * self.sd + self.mu)
 
+    def host_params(self) -> np.ndarray:
+        return self.params.cpu().numpy().astype(np.float32)
+
+    def install(self, margin: float = 0.0) -> None:
+        """Hand the trained network to the library as its cost model (the
+        library then evaluates it per class with its own forward kernel and
+        consults it under the MODEL selector mode)."""
+        if self.mu is None:
+            raise RuntimeError("the network has not been fitted")
+        sbgemm.set_cost_model(self.F, self.H, self.V, self.host_params(), self.mu, self.sd, margin)
+
+    def save(self, path: str, margin: float = 0.0) -> None:
+        """Install the network and write it to a versioned cost-model file
+        that any process can load (``sbgemm_load_cost_model`` or the
+        SBGEMM_COST_MODEL environment setting)."""
+        self.install(margin)
+        sbgemm.save_cost_model(path)
+
     def choose(self, feats: np.ndarray, nvalid: np.ndarray, margin: float = 0.0,
                defaults: np.ndarray | None = None) -> np.ndarray:
         """The variant with the smallest predicted time, unless it is not
@@ -361,13 +379,11 @@ class CostModel:
 
 
 def default_choices(classes) -> np.ndarray:
-    """The library's own choice for each class without a selection table
-    (``sbgemm_get_choice`` on an empty table: the tensor-core variant of the
-    16-bit types at m = n = k = 8, 16; variant 2 for complex64 and for fp32
-    below 1e6 pairs; variant 0 otherwise)."""
-    sbgemm.clear_choices()
-    return np.array([sbgemm.get_choice(c[0], c[1], c[2], c[3], c[4], c[5], c[7],
-                                       size_class(c[8])) for c in classes], dtype=np.int64)
+    """The library's built-in choice for each class (``sbgemm_default_variant``:
+    the tensor-core variant of the 16-bit types at m = n = k = 8, 16; variant
+    2 for complex64 and for fp32 below 1e6 pairs; variant 0 otherwise)."""
+    return np.array([sbgemm.default_variant(c[0], c[1], c[2], c[3], size_class(c[8]))
+                     for c in classes], dtype=np.int64)
 
 
 def table_from_db(rows):
@@ -475,10 +491,14 @@ def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=9, steps=3000, db_p
     return rep, net
 
 
-def install(classes, choices) -> None:
-    """Write choices into the library's selection table."""
+def install(classes, choices, path: str | None = None) -> None:
+    """Write choices into the library's selection table, and the whole table
+    to `path` when given (loadable by any process: ``sbgemm_load_table`` or
+    the SBGEMM_TABLE environment setting)."""
     for (dtype, m, n, k, ta, tb, conj, beta0, N), v in zip(classes, choices):
         sbgemm.set_choice(dtype, m, n, k, ta, tb, beta0, size_class(N), int(v))
+    if path:
+        sbgemm.save_table(path)
 
 
 if __name__ == "__main__":

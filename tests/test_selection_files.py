@@ -1,0 +1,165 @@
+"""Host-only checks of variant selection across processes: the selection
+table and cost-model files round-trip through the C ABI, malformed files
+are rejected without side effects, the selector modes decide which source
+a class's choice comes from, and the environment settings are applied in a
+fresh process.  No GPU: the cost model is installed while the mode is not
+MODEL, so it is not evaluated here (the GPU test does that)."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1304_7053_gb300 import sbgemm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+S, D, C, Z, H, B = range(6)
+
+
+@pytest.fixture(autouse=True)
+def clean_state():
+    sbgemm.set_selector(sbgemm.SELECTOR_TABLE)
+    sbgemm.clear_choices()
+    yield
+    sbgemm.set_selector(sbgemm.SELECTOR_TABLE)
+    sbgemm.clear_choices()
+
+
+ENTRIES = [(S, 10, 10, 10, 0, 0, 1, 5, 4), (D, 16, 16, 16, 1, 0, 0, 6, 3),
+           (H, 12, 12, 12, 0, 0, 1, 6, 7), (C, 9, 16, 9, 1, 0, 0, 5, 6)]
+
+
+def test_table_file_round_trip(tmp_path):
+    L = sbgemm.lib()
+    for e in ENTRIES:
+        assert L.sbgemm_set_choice(*e) == 0
+    p = str(tmp_path / "table.txt")
+    sbgemm.save_table(p)
+    lines = open(p).read().splitlines()
+    assert lines[0] == "sbgemm-table 1" and lines[1].startswith("device ")
+    sbgemm.clear_choices()
+    for e in ENTRIES:
+        assert L.sbgemm_get_choice(*e[:8]) == L.sbgemm_default_variant(e[0], e[1], e[2], e[3], e[7])
+    sbgemm.load_table(p)
+    for e in ENTRIES:
+        assert L.sbgemm_get_choice(*e[:8]) == e[8]
+    p2 = str(tmp_path / "table2.txt")
+    sbgemm.save_table(p2)
+    assert open(p2).read() == open(p).read()
+
+
+@pytest.mark.parametrize("body", [
+    "sbgemm-table 2\n",                                    # unknown version
+    "not a table\n0 10 10 10 0 0 1 5 4\n",                # no header
+    "sbgemm-table 1\n0 10 10 10 0 0 1 5 99\n",            # variant out of range
+    "sbgemm-table 1\n0 17 10 10 0 0 1 5 0\n",             # m out of range
+    "sbgemm-table 1\n0 10 10 10 0 0 1 9 0\n",             # size class out of range
+    "sbgemm-table 1\n0 10 10 10 0 0 1 5\n",               # missing field
+    "sbgemm-table 1\n0 10 10 10 0 0 1 5 2 7\n",           # extra field
+])
+def test_malformed_table_is_rejected_and_adds_nothing(tmp_path, body):
+    p = str(tmp_path / "bad.txt")
+    # a valid entry first: nothing of the file may be added
+    open(p, "w").write(body if not body.startswith("sbgemm-table 1") else
+                       body.replace("sbgemm-table 1\n", "sbgemm-table 1\n3 8 8 8 0 0 0 5 5\n"))
+    assert sbgemm.lib().sbgemm_load_table(p.encode()) == -9
+    assert sbgemm.lib().sbgemm_get_choice(Z, 8, 8, 8, 0, 0, 0, 5) == \
+        sbgemm.lib().sbgemm_default_variant(Z, 8, 8, 8, 5)
+    assert sbgemm.lib().sbgemm_load_table(str(tmp_path / "missing.txt").encode()) == -9
+
+
+def test_selector_modes():
+    L = sbgemm.lib()
+    assert L.sbgemm_set_choice(S, 10, 10, 10, 0, 0, 1, 5, 4) == 0
+    assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == 4
+    sbgemm.set_selector(sbgemm.SELECTOR_DEFAULT)
+    assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == L.sbgemm_default_variant(S, 10, 10, 10, 5)
+    assert sbgemm.get_selector()[0] == sbgemm.SELECTOR_DEFAULT
+    sbgemm.set_selector(sbgemm.SELECTOR_TABLE)
+    assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == 4
+    assert L.sbgemm_set_selector(7) == -5
+    # the built-in rule itself
+    assert L.sbgemm_default_variant(H, 16, 16, 16, 6) == 7
+    assert L.sbgemm_default_variant(H, 12, 12, 12, 6) == 0
+    assert L.sbgemm_default_variant(C, 10, 10, 10, 6) == 2
+    assert L.sbgemm_default_variant(S, 10, 10, 10, 5) == 2
+    assert L.sbgemm_default_variant(S, 10, 10, 10, 6) == 0
+    assert L.sbgemm_default_variant(D, 10, 10, 10, 5) == 0
+    assert L.sbgemm_default_variant(S, 7, 3, 11, 5) == 0
+    assert L.sbgemm_default_variant(S, 17, 3, 11, 5) == -1
+
+
+def _params(seed=3):
+    n = int(sbgemm.lib().sbgemm_mlp_param_count(16, 64, 9))
+    return ((np.arange(n) * 2654435761 % 1000003) / 1000003.0 - 0.5).astype(np.float32)
+
+
+def test_cost_model_file_round_trip(tmp_path):
+    p = _params()
+    sbgemm.set_cost_model(16, 64, 9, p, -2.5, 1.25, 0.05)
+    f1 = str(tmp_path / "model.txt")
+    sbgemm.save_cost_model(f1)
+    txt = open(f1).read().split("\n")
+    assert txt[0] == "sbgemm-cost-model 1" and txt[1].startswith("device ")
+    assert txt[2] == "features 16 hidden 64 outputs 9"
+    vals = np.array(" ".join(txt[5:]).split(), dtype=np.float32)
+    assert np.array_equal(vals, p)                        # 9 digits: exact for fp32
+    sbgemm.load_cost_model(f1)
+    f2 = str(tmp_path / "model2.txt")
+    sbgemm.save_cost_model(f2)
+    assert open(f2).read() == open(f1).read()
+
+
+def test_cost_model_rejections(tmp_path):
+    L = sbgemm.lib()
+    p = _params()
+    addr = p.ctypes.data
+    assert L.sbgemm_set_cost_model(15, 64, 9, addr, 0.0, 1.0, 0.0) == -5     # F must be 16
+    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 0.0, 0.0) == -5     # std > 0
+    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 1.0, 1.0) == -5     # margin < 1
+    q = p.copy()
+    q[5] = np.nan
+    assert L.sbgemm_set_cost_model(16, 64, 9, q.ctypes.data, 0.0, 1.0, 0.0) == -5
+    sbgemm.set_cost_model(16, 64, 9, p, 0.0, 1.0, 0.0)
+    good = str(tmp_path / "m.txt")
+    sbgemm.save_cost_model(good)
+    text = open(good).read()
+    n = int(L.sbgemm_mlp_param_count(16, 64, 9))
+    for bad in (text.replace(f"params {n}", f"params {n - 1}"),        # count mismatch
+                text.replace("sbgemm-cost-model 1", "sbgemm-cost-model 3"),
+                text.rsplit("\n", 2)[0] + "\n",                          # truncated
+                text + "1.0\n"):                                         # trailing value
+        f = str(tmp_path / "bad.txt")
+        open(f, "w").write(bad)
+        assert L.sbgemm_load_cost_model(f.encode()) == -9
+
+
+def test_environment_settings_in_a_fresh_process(tmp_path):
+    L = sbgemm.lib()
+    assert L.sbgemm_set_choice(S, 10, 10, 10, 0, 0, 1, 5, 4) == 0
+    p = str(tmp_path / "t.txt")
+    sbgemm.save_table(p)
+    code = ("import json, sys; sys.path.insert(0, %r)\n"
+            "from paper_1304_7053_gb300 import sbgemm\n"
+            "L = sbgemm.lib()\n"
+            "print(json.dumps([sbgemm.get_selector(), L.sbgemm_get_choice(0, 10, 10, 10, 0, 0, 1, 5)]))"
+            % ROOT)
+
+    def run(**env):
+        e = {k: v for k, v in os.environ.items() if not k.startswith("SBGEMM_")}
+        e.update(env)
+        r = subprocess.run([sys.executable, "-c", code], env=e, capture_output=True, text=True,
+                           timeout=120)
+        assert r.returncode == 0, r.stderr
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    dflt = L.sbgemm_default_variant(S, 10, 10, 10, 5)
+    assert run() == [[1, 0], dflt]
+    assert run(SBGEMM_TABLE=p) == [[1, 0], 4]
+    assert run(SBGEMM_TABLE=p, SBGEMM_SELECTOR="default") == [[0, 0], dflt]
+    assert run(SBGEMM_TABLE=str(tmp_path / "none.txt")) == [[1, -9], dflt]
+    assert run(SBGEMM_SELECTOR="model") == [[1, -5], dflt]        # no model: mode unchanged
