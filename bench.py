@@ -456,7 +456,8 @@ def run_vbatch_bench(dtype, dev, stream, reps=20, warm=3, N=1_000_000):
     # the plan's bucketing window, tuned on this batch by the autotuner
     from paper_1304_7053_gb300 import selector
     problems = sbgemm.vproblems_from_desc(desc)
-    window, wtimes = selector.tune_vbatch(dtype, problems, A, B, C, windows=(0, 262144, 65536),
+    window, wtimes = selector.tune_vbatch(dtype, problems, A, B, C,
+                                          windows=(selector.WHOLE_BATCH, 262144, 65536, 16384),
                                           reps=3, stream=stream)
     plan = sbgemm.VPlan(dtype, problems)
     sbgemm.lib().sbgemm_vbatch_config(0)
@@ -504,8 +505,9 @@ def run_vbatch_bench(dtype, dev, stream, reps=20, warm=3, N=1_000_000):
     torch.cuda.synchronize()
     f_ms = f0.elapsed_time(f1) / reps
     return {"dtype": dtype, "problems": N, "tiles": info["tiles"], "buckets": info["buckets"],
-            "window": "whole batch" if window == 0 else window,
-            "window_trials_ms": {("whole" if w == 0 else str(w)): round(t, 4) for w, t in wtimes.items()},
+            "window": "whole batch" if window == selector.WHOLE_BATCH else window,
+            "window_trials_ms": {("whole" if w == selector.WHOLE_BATCH else str(w)): round(t, 4)
+                                 for w, t in wtimes.items()},
             "ms": round(v_ms, 4), "gflops": round(flops / (v_ms * 1e-3) / 1e9, 1),
             "gbps": round(alg_bytes / (v_ms * 1e-3) / 1e9, 1),
             "fixed_per_size_ms": round(f_ms, 4),

@@ -433,11 +433,11 @@ sbgemm_status sbgemm_vbatch_plan_destroy(sbgemm_vplan plan);
 /*
  * Bucketing window of the plans created after this call: problems are
  * bucketed within windows of `window` consecutive problems and the tiles
- * are queued window by window (neighbours in the arenas, which may share
- * memory sectors, are then processed close in time, at the price of blocks
- * switching between size-specialised code more often).  0 restores the
- * default, one window for the whole batch.  Process-wide; negative values
- * give SBGEMM_ERR_INVALID_VALUE.
+ * are queued window by window, so neighbours in the arenas (which may share
+ * memory sectors) are processed close in time and those sectors are read
+ * from DRAM once.  0 restores the default, 65,536 problems; a window of at
+ * least the problem count buckets the whole batch at once.  Process-wide;
+ * negative values give SBGEMM_ERR_INVALID_VALUE.
  */
 sbgemm_status sbgemm_vbatch_config(int window);
 

@@ -303,7 +303,7 @@ __host__ __device__ constexpr int pick_vec(int es, int a, int b, int c) {
 // The tile of each (type, shape, op) comes from the cost model in
 // gen_tiles.py (tile_table.h); the vector widths below follow the same rules.
 template <class Ty_, int M_, int N_, int K_, bool TA_, bool TB_, int TM_, int TN_,
-          bool SI_, bool SJ_, int NT_>
+          bool SI_, bool SJ_, int NT_, int UL_ = 0>
 struct Cfg {
     using Ty = Ty_;
     using S = typename Ty::S;
@@ -337,8 +337,8 @@ struct Cfg {
     // l-chunks per unrolled body of the product loop: about 128 FMAs per
     // body, so the large shapes keep a short loop instead of one fully
     // unrolled body (smaller code, fewer instruction-cache misses when
-    // several shapes share one kernel)
-    static constexpr int UL = (TM * TN * VL >= 128) ? 1 : (128 / (TM * TN * VL));
+    // several shapes share one kernel); UL_ > 0 sets it explicitly
+    static constexpr int UL = UL_ > 0 ? UL_ : (TM * TN * VL >= 128) ? 1 : (128 / (TM * TN * VL));
 };
 
 // ------------------------------------------------------------ staging

@@ -34,11 +34,14 @@ constexpr int kVKinds = 17;
 constexpr int kVGeneric = 16;
 constexpr int kVThreads = 128;
 constexpr int kVMaxTile = 128;
-// problems per bucketing window of a plan: by default the whole batch, so
-// each bucket's tiles are contiguous in the queue and all blocks run the
-// same size-specialised code at once (windows of 4096 problems made the
-// blocks switch kinds nearly every tile: 1.8x slower on the fp32 mix)
-constexpr int kVDefaultWindow = 1 << 30;
+// Problems per bucketing window of a plan.  Arena neighbours share 32-byte
+// memory sectors at their boundaries; bucketing the whole batch at once put
+// neighbours of different sizes far apart in time, and DRAM read those
+// sectors twice (1.40x the algorithmic bytes on the fp32 mix).  Windows of
+// 65,536 problems (about 42 MB of fp32 operands, well inside the 129 MB L2)
+// keep them close: 0.99x, and the fastest window of a sweep over
+// whole / 262,144 / 65,536 / 16,384 / 4,096 for fp32 and fp64.
+constexpr int kVDefaultWindow = 1 << 16;
 
 // Pipeline shape per storage type: two stages (one tile in flight while
 // another computes).  Memory-bound types take 28 KB stages and three blocks
@@ -71,11 +74,17 @@ struct VArgs {
 };
 
 // The specialised configuration of square size s (op N/N); kinds whose
-// tile needs another block size fall back to the generic kind.
+// tile needs another block size fall back to the generic kind.  The product
+// loop is not unrolled (one l-chunk per iteration) and neither are the copy
+// loops: a block switches between the 16 size-specialised bodies from tile to
+// tile, and with fully unrolled bodies (about 3x the code) instruction fetch
+// bounded the kernel whenever neighbouring tiles had different sizes; with
+// the short bodies, bucketing windows that keep arena neighbours close in
+// time cost nothing (fp32 mix: windows of 4096 problems 0.438 -> 0.241 ms).
 template <class Ty, int s>
 struct VKindCfg {
     static constexpr TileEntry te = tile_for(Ty::code, s, s, s, 0, 0);
-    using Cf = Cfg<Ty, s, s, s, false, false, te.tm, te.tn, te.si != 0, te.sj != 0, te.nt>;
+    using Cf = Cfg<Ty, s, s, s, false, false, te.tm, te.tn, te.si != 0, te.sj != 0, te.nt, 1>;
     static constexpr bool ok = te.nt == kVThreads;
 };
 
@@ -125,12 +134,12 @@ __device__ __forceinline__ void vcopy_square(S* dst, const S* src, int l0) {
     if constexpr ((SE * ES) % 16 == 0) {
         constexpr int CPM = SE * ES / 16, EPC = 16 / ES;
         if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-#pragma unroll
+#pragma unroll 1
             for (int c = l0; c < CPM; c += LPP) cp_async16(dst + c * EPC, src + c * EPC, 16);
             return;
         }
     }
-#pragma unroll
+#pragma unroll 1
     for (int e = l0; e < SE; e += LPP) vcopy_elem<S, ES>(dst + e, src + e);
 }
 
@@ -199,13 +208,13 @@ __device__ __forceinline__ void vstore_fixed(S* gC, const S* sC, const VRec* rec
         if constexpr ((SE * ES) % 16 == 0) {
             constexpr int CPM = SE * ES / 16, EPC = 16 / ES;
             if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-#pragma unroll
+#pragma unroll 1
                 for (int c = l0; c < CPM; c += LPP)
                     *reinterpret_cast<uint4*>(dst + c * EPC) = *reinterpret_cast<const uint4*>(src + c * EPC);
                 continue;
             }
         }
-#pragma unroll
+#pragma unroll 1
         for (int e = l0; e < SE; e += LPP) dst[e] = src[e];
     }
 }

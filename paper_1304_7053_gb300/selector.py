@@ -184,13 +184,16 @@ def _time_calls(fn, reps: int, stream) -> float:
     return ts[len(ts) // 2]
 
 
+WHOLE_BATCH = 1 << 30     # a bucketing window that holds any batch
+
+
 def tune_vbatch(dtype: str, problems, A, B, C, alpha=1.0, beta=1.0,
-                windows=(0, 262144, 65536, 16384), reps=5, stream=None):
+                windows=(WHOLE_BATCH, 262144, 65536, 16384), reps=5, stream=None):
     """Exhaustive tuning of a variable-size batch's bucketing window: one
     plan per window, `reps` timed runs each; the fastest window is installed
     process-wide (``sbgemm_vbatch_config``) for the plans created after this
-    call.  Returns (best window, {window: ms}); window 0 is the whole batch.
-    C is overwritten by the trial runs."""
+    call.  Returns (best window, {window: ms}); ``WHOLE_BATCH`` buckets the
+    whole batch at once.  C is overwritten by the trial runs."""
     import torch
     stream = stream or torch.cuda.current_stream()
     L = sbgemm.lib()
