@@ -75,12 +75,14 @@ struct VArgs {
 
 // The specialised configuration of square size s (op N/N); kinds whose
 // tile needs another block size fall back to the generic kind.  The product
-// loop is not unrolled (one l-chunk per iteration) and neither are the copy
-// loops: a block switches between the 16 size-specialised bodies from tile to
-// tile, and with fully unrolled bodies (about 3x the code) instruction fetch
-// bounded the kernel whenever neighbouring tiles had different sizes; with
-// the short bodies, bucketing windows that keep arena neighbours close in
-// time cost nothing (fp32 mix: windows of 4096 problems 0.438 -> 0.241 ms).
+// loop is not unrolled (one l-chunk per iteration) and neither are the
+// staging copy loops: a block switches between the 16 size-specialised
+// bodies from tile to tile, and with fully unrolled bodies (about 3x the
+// code) instruction fetch bounded the kernel whenever neighbouring tiles had
+// different sizes; with the short bodies, bucketing windows that keep arena
+// neighbours close in time cost nothing (fp32 mix: windows of 4096 problems
+// 0.438 -> 0.241 ms).  The C write-back loops stay unrolled (rolling them
+// measured 6% slower).
 template <class Ty, int s>
 struct VKindCfg {
     static constexpr TileEntry te = tile_for(Ty::code, s, s, s, 0, 0);
@@ -208,13 +210,13 @@ __device__ __forceinline__ void vstore_fixed(S* gC, const S* sC, const VRec* rec
         if constexpr ((SE * ES) % 16 == 0) {
             constexpr int CPM = SE * ES / 16, EPC = 16 / ES;
             if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-#pragma unroll 1
+#pragma unroll
                 for (int c = l0; c < CPM; c += LPP)
                     *reinterpret_cast<uint4*>(dst + c * EPC) = *reinterpret_cast<const uint4*>(src + c * EPC);
                 continue;
             }
         }
-#pragma unroll 1
+#pragma unroll
         for (int e = l0; e < SE; e += LPP) dst[e] = src[e];
     }
 }
