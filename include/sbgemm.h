@@ -268,8 +268,14 @@ sbgemm_status sbgemm_gemm_multi_nounif(int type, char transa, char transb, int m
 /* Kernel variants (used by the autotuner and the learned selector).   */
 /* ------------------------------------------------------------------ */
 
-/* Number of kernel variants a (type, m, n, k) problem can run with; variant
- * 0 is always the default choice.  Returns 0 for an invalid request. */
+/* Number of kernel variants a (type, m, n, k) problem can run with (0 for
+ * an invalid request).  Shapes with specialised kernels have six settings of
+ * the pipelined kernel (0..5) and the generic kernel (6); the 16-bit types at
+ * m = n = k = 8, 12, 16 and real fp64 add variant 7, the tensor-core kernel
+ * (for fp64: operands split into exact 8-bit digits whose products run on
+ * the binary16 MMA path, recombined exactly; entries whose accuracy the
+ * split cannot guarantee are recomputed with fp64 FMAs).  Other shapes have
+ * the generic kernel only. */
 int sbgemm_num_variants(int type, int m, int n, int k);
 
 /* Human-readable description of a variant (static storage, never NULL). */
@@ -300,8 +306,8 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
  *   SBGEMM_SELECTOR_MODEL: the table's entry, else the installed cost
  *     model's choice, else the built-in rule.
  * Built-in rule: the tensor-core variant (7) for the 16-bit types at
- * m = n = k = 8 and 16; variant 2 for complex64, and for fp32 with
- * size_class <= 5; variant 0 otherwise.
+ * m = n = k = 8 and 16 and for real fp64 at m = n = k >= 13; variant 2 for
+ * complex64, and for fp32 with size_class <= 5; variant 0 otherwise.
  * All of this is process-wide host state: set it before issuing work, not
  * concurrently with calls that read it.
  *

@@ -307,7 +307,7 @@ const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
         "pipe tile32K st2 occ-max", "pipe tile16K st3 1cta/sm (st2 for fp64)",
         "pipe tile4K st4 occ-max", "pipe tile24K st3 2cta/sm",
         "generic thread-per-entry",
-        "tensor-core mma.sync (16-bit, N/N, flat; else variant 0)"};
+        "tensor-core: mma.sync for 16-bit N/N flat; 8-bit digit products for fp64; else variant 0"};
     const int nv = sbgemm_num_variants(type, m, n, k);
     if (variant < 0 || variant >= nv) return "invalid";
     return names[sbg::internal_variant(m, n, k, variant)];

@@ -14,6 +14,7 @@ SBG_DECL(S) SBG_DECL(D) SBG_DECL(C) SBG_DECL(Z) SBG_DECL(H) SBG_DECL(B)
         sbgemm_status st;                                                  \
         if (r.variant == kMmaVariant) {                                    \
             if (mma16_ok(r)) return run_mma16(r);                          \
+            if (ozaki_ok(r)) return run_ozaki(r);                          \
             Req r0 = r;                                                    \
             r0.variant = 0;                                                \
             return run_##T(r0);                                            \

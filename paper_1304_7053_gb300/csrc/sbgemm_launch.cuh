@@ -42,11 +42,16 @@ struct LaunchOpts {
 // mapping of the paper's first method in Section 6).
 constexpr int kNumPipeVariants = 6;
 // Variant after the generic kernel: the tensor-core kernel of the 16-bit
-// types (csrc/mma16.cuh), for m = n = k = 8, 12 or 16, op N/N, flat layouts; any
-// other request given this variant runs variant 0.
+// types (csrc/mma16.cuh), for m = n = k = 8, 12 or 16, op N/N, flat layouts,
+// and of real fp64 (csrc/ozaki.cuh, any op and layout of the uniform form);
+// any other request given this variant runs variant 0.
 constexpr int kMmaVariant = kNumPipeVariants + 1;
 sbgemm_status run_mma16(const Req& r);   // mma16.cu
 bool mma16_ok(const Req& r);
+// The same variant index for real fp64 runs the tensor-core kernel that
+// splits fp64 operands into exact 8-bit digits (csrc/ozaki.cuh).
+sbgemm_status run_ozaki(const Req& r);   // ozaki.cu
+bool ozaki_ok(const Req& r);
 inline LaunchOpts pipe_variant(int v, int type_code = 0) {
     // fp64 types are bound by the fp64 pipe, not by memory: two stages are
     // enough and leave room for more computing warps

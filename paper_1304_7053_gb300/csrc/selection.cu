@@ -52,7 +52,10 @@ CostModel g_model;
 std::once_flag g_env_once;
 std::atomic<int> g_env_status{0};
 
+// the tensor-core variant: 16-bit storage at m = n = k = 8, 12, 16, and real
+// fp64 (digit-split products) on every shape with specialised kernels
 bool has_mma_variant(int type, int m, int n, int k) {
+    if (type == SBGEMM_TYPE_D) return has_specialized(0, m, n, k);
     return (type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && m == n && n == k &&
            (m == 8 || m == 12 || m == 16);
 }
@@ -334,10 +337,16 @@ int variants_for(int type, int m, int n, int k) {
 //   square N/N sizes 2..16 it took 9% less total time than variant 0 for
 //   complex64 at N = 1e5 and 1e6, and 5% less for fp32 at N = 1e5 (up to 20%
 //   per size), while fp32 at N = 1e6 measured the same total;
+// - the tensor-core kernel (digit-split products) for real fp64 at
+//   m = n = k >= 13: at N = 1e5 it took 410 / 409 / 406 / 378 us for
+//   m = 13 / 14 / 15 / 16 against 465 / 471 / 624 / 685 us on the fp64 FMA
+//   pipe (1.14-1.81x; below m = 13 the FMA kernels win, as the tensor-core
+//   kernel always computes a 16 x 16 x 16 product);
 // - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
 //   no difference; the 16-bit CUDA-core kernels were mixed).
 int default_variant(int type, int m, int n, int k, int sc) {
-    if (has_mma_variant(type, m, n, k) && m != 12) return kMmaVariant;
+    if (type == SBGEMM_TYPE_D && m == n && n == k && m >= 13) return kMmaVariant;
+    if (has_mma_variant(type, m, n, k) && type != SBGEMM_TYPE_D && m != 12) return kMmaVariant;
     if (!has_specialized(0, m, n, k)) return 0;
     if (type == SBGEMM_TYPE_C || (type == SBGEMM_TYPE_S && sc <= 5)) return 2;
     return 0;

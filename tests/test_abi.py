@@ -100,7 +100,8 @@ def test_variant_table_host_logic():
     assert "generic" in sbgemm.variant_name("s", 7, 3, 11, 0)
     # the 16-bit types at m = n = k = 8, 16 also have the tensor-core variant
     assert sbgemm.num_variants("b", 16, 16, 16) == 8 and sbgemm.num_variants("h", 8, 8, 8) == 8
-    assert sbgemm.num_variants("b", 12, 12, 12) == 8 and sbgemm.num_variants("d", 16, 16, 16) == 7
+    assert sbgemm.num_variants("b", 12, 12, 12) == 8 and sbgemm.num_variants("d", 16, 16, 16) == 8
+    assert sbgemm.num_variants("z", 16, 16, 16) == 7 and sbgemm.num_variants("d", 9, 16, 9) == 8
     assert sbgemm.num_variants("h", 10, 10, 10) == 7
     assert "tensor-core" in sbgemm.variant_name("h", 16, 16, 16, 7)
     sbgemm.clear_choices()
@@ -111,6 +112,9 @@ def test_variant_table_host_logic():
     assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 6) == 0
     assert sbgemm.get_choice("c", 10, 10, 10, 0, 0, 1, 6) == 2
     assert sbgemm.get_choice("d", 10, 10, 10, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 7
+    assert sbgemm.get_choice("d", 12, 12, 12, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("h", 16, 16, 16, 0, 0, 1, 6) == 7
     assert sbgemm.get_choice("h", 12, 12, 12, 0, 0, 1, 6) == 0
     assert sbgemm.get_choice("s", 7, 3, 11, 0, 0, 1, 5) == 0

@@ -1,0 +1,100 @@
+"""Real fp64 on the tensor cores (variant 7 of the d shapes with specialised
+kernels): operands split into exact 8-bit digits, digit products on the fp16
+MMA path, recombined exactly in integers.  Held to the same oracle checks as
+the fp64 FMA kernels: bit-exact on small-integer inputs, within the
+elementwise bound of gpu_helpers on uniform[-1, 1] inputs, and within the
+bound on inputs whose rows and columns span many binades (the entries the
+emulation cannot bound fall back to fp64 FMAs inside the kernel)."""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_1304_7053_gb300 import inputs
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+TC = 7
+OPS = [("N", "N"), ("T", "N"), ("N", "T"), ("C", "C")]
+
+
+@pytest.mark.parametrize("m", list(range(1, 17)))
+def test_integer_inputs_bit_exact(m):
+    for (ta, tb), beta in itertools.product(OPS, (0.0, -0.5)):
+        b = inputs.UniformBatch("d", ta, tb, m, m, m, 1237, seed=300 + m, int_valued=True)
+        got = H.run_gpu(b, 1.5, beta, variant=TC)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, beta), 1.5, beta, exact=True)
+
+
+@pytest.mark.parametrize("m", list(range(1, 17)))
+def test_uniform_inputs_within_bound(m):
+    for (ta, tb), beta in itertools.product(OPS, (0.0, -0.5)):
+        b = inputs.UniformBatch("d", ta, tb, m, m, m, 1031, seed=400 + m)
+        got = H.run_gpu(b, 1.5, beta, variant=TC)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, beta), 1.5, beta)
+
+
+@pytest.mark.parametrize("shape", [(4, 16, 4), (9, 16, 9), (16, 8, 16), (3, 9, 3), (16, 16, 1)])
+def test_fem_shapes_and_padded_layout(shape):
+    m, n, k = shape
+    b = inputs.UniformBatch("d", "T", "N", m, n, k, 2003, seed=17)
+    H.assert_parity(b, H.run_gpu(b, 1.0, 1.0, variant=TC), H.oracle_ref(b, 1.0, 1.0), 1.0, 1.0)
+    bp = inputs.UniformBatch("d", "N", "T", m, n, k, 999, seed=18, pad_ld=2, pad_ld2=5)
+    H.assert_parity(bp, H.run_gpu(bp, 1.5, -0.5, variant=TC), H.oracle_ref(bp, 1.5, -0.5), 1.5, -0.5)
+
+
+def _wide_range(b, seed):
+    """Scale every entry of A and B by 2^e, e uniform in -60..0, so rows and
+    columns mix entries of very different sizes."""
+    for name, s in (("A", seed), ("B", seed + 1)):
+        x = getattr(b, name)
+        e = (inputs.splitmix64(s, x.size) % np.uint64(61)).astype(np.int64)
+        setattr(b, name, np.ldexp(x, -e))
+
+
+@pytest.mark.parametrize("m", [4, 9, 16])
+def test_wide_dynamic_range_within_bound(m):
+    """Entries spanning 60 binades: many outputs fail the emulation's own
+    accuracy test and take the fp64 FMA path; every output meets the bound."""
+    for ta, tb in (("N", "N"), ("T", "T")):
+        b = inputs.UniformBatch("d", ta, tb, m, m, m, 2001, seed=500 + m)
+        _wide_range(b, 700 + m)
+        got = H.run_gpu(b, 1.5, -0.5, variant=TC)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
+
+
+def test_extreme_exponents_and_special_values():
+    """Rows scaled near the top and bottom of the fp64 range (subnormal
+    products), a zero row, and pairs with NaN or Inf: finite results within
+    the bound, non-finite positions as the FMA kernel gives them."""
+    m, N = 8, 64
+    b = inputs.UniformBatch("d", "N", "N", m, m, m, N, seed=601)
+    A = b.A.reshape(N, m * m)
+    B = b.B.reshape(N, m * m)
+    A[0] *= 2.0 ** 500
+    B[0] *= 2.0 ** 500
+    A[1] *= 2.0 ** -540
+    B[1] *= 2.0 ** -540
+    A[2, :m] = 0.0               # column 0 of pair 2's A
+    A[3, 5] = np.nan
+    B[4, 7] = np.inf
+    got = H.run_gpu(b, 1.0, 0.0, variant=TC)
+    ref_fma = H.run_gpu(b, 1.0, 0.0, variant=0)
+    g, r = got.reshape(N, -1), ref_fma.reshape(N, -1)
+    assert np.array_equal(np.isnan(g), np.isnan(r)) and np.array_equal(np.isinf(g), np.isinf(r))
+    fin = np.ones(N, dtype=bool)
+    fin[[3, 4]] = False
+    sub = inputs.UniformBatch("d", "N", "N", m, m, m, int(fin.sum()), seed=0)
+    sub.A = A[fin].ravel().copy()
+    sub.B = B[fin].ravel().copy()
+    sub.C = b.C.reshape(N, -1)[fin].ravel().copy()
+    H.assert_parity(sub, g[fin].ravel().copy(), H.oracle_ref(sub, 1.0, 0.0), 1.0, 0.0)
+
+
+def test_device_scalars_and_default_selection():
+    b = inputs.UniformBatch("d", "N", "N", 16, 16, 16, 3001, seed=77)
+    got = H.run_gpu(b, 1.5, -0.5, variant=TC, device_scalars=True)
+    H.assert_parity(b, got, H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
