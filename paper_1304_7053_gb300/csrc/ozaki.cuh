@@ -29,9 +29,11 @@
 // a lower bound of (|A||B|)_ij 2^(14 - e_i - f_j); T_ij >= 512 guarantees
 // that the emulation error is at most (k/2) u (|A||B|)_ij (u = 2^-53), so the
 // result meets the elementwise bound (k/2 + 3) u (|alpha||A||B| + |beta||C|)
-// including the final roundings.  Entries that fail the test (an output
-// whose row and column are dominated by entries of very different sizes), and
-// every pair with a non-finite input, are recomputed with fp64 FMAs.
+// including the final roundings.  Entries that fail the test (an output whose
+// row and column are dominated by entries of very different sizes, or whose
+// row of op(A) or column of op(B) is zero or subnormal), and every pair with
+// a non-finite input, are recomputed with fp64 FMAs: always correct, at the
+// fp64 pipe's speed for those entries.
 //
 // One warp computes one pair (a 16 x 16 x 16 product; smaller shapes read
 // zeros outside m x k and k x n); a persistent grid of warps walks the batch.
@@ -336,8 +338,9 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
                 const int j = 2 * tq + (r & 1) + 8 * h;
                 if (i >= m || j >= n) continue;
                 double v;
-                if ((use >> r) & 1u) {
-                    v = oz_assemble(shi[r], slo[r], (r >> 1 ? ea1 : ea0) + ecol[h][r & 1] - 38);
+                const int er = r >> 1 ? ea1 : ea0, ec = ecol[h][r & 1];
+                if (!nonfinite && ((use >> r) & 1u)) {
+                    v = oz_assemble(shi[r], slo[r], er + ec - 38);
                 } else {
                     // fp64 FMAs for this entry (inputs out of the emulation's range)
                     v = 0.0;

@@ -50,8 +50,11 @@ CPLX = {"c", "z"}
 
 
 class Pools:
-    """Reusable device buffers filled once with uniform[-1, 1) fp32 values
-    (other types read the same bytes; timing does not depend on values)."""
+    """Reusable device buffers filled once with uniform[-1, 1) values: fp32
+    for the s, c and 16-bit types (which read the same bytes; their kernels'
+    timing does not depend on the values) and fp64 for d and z, whose
+    tensor-core kernel takes its fp64-FMA path for entries of very different
+    sizes (fp32 bytes read as fp64 are such entries)."""
 
     def __init__(self, max_bytes, dev):
         import torch
@@ -62,8 +65,18 @@ class Pools:
         self.A = torch.rand(n, device=dev, generator=g) * 2 - 1
         self.B = torch.rand(n, device=dev, generator=g) * 2 - 1
         self.C = torch.rand(n, device=dev, generator=g) * 2 - 1
+        n64 = (max_bytes + 7) // 8
+        self.A64 = torch.rand(n64, device=dev, generator=g, dtype=torch.float64) * 2 - 1
+        self.B64 = torch.rand(n64, device=dev, generator=g, dtype=torch.float64) * 2 - 1
+        self.C64 = torch.rand(n64, device=dev, generator=g, dtype=torch.float64) * 2 - 1
         self.flush = torch.ones(256 << 20, dtype=torch.uint8, device=dev)
         self._sink = torch.empty((), dtype=torch.int64, device=dev)
+
+    def for_type(self, dtype):
+        """(A, B, C) buffers holding values of the type's precision."""
+        if dtype in ("d", "z"):
+            return self.A64, self.B64, self.C64
+        return self.A, self.B, self.C
 
     def evict(self):
         """Read the 256 MB flush buffer (L2 ends cold and clean)."""
@@ -88,6 +101,7 @@ def time_ours(pools, dtype, ta, tb, m, n, k, N, alpha, beta, reps, variant=None,
     br, bc = (k, n) if opb == "N" else (n, k)
     lda2 = 0 if shared_a else ar * ac
     L = sbgemm.lib()
+    pA, pB, pC = pools.for_type(dtype)
     ab, bb = sbgemm._scalar_buf(dtype, alpha), sbgemm._scalar_buf(dtype, beta)
     if variant is None:
         variant = sbgemm.get_choice(dtype, m, n, k, opa != "N", opb != "N", complex(beta) == 0,
@@ -95,9 +109,9 @@ def time_ours(pools, dtype, ta, tb, m, n, k, N, alpha, beta, reps, variant=None,
     ms = ctypes.c_float()
     s = pools.torch.cuda.current_stream().cuda_stream
     st = L.sbgemm_time_variant(sbgemm.TYPE_CODES[dtype], opa.encode(), opb.encode(), m, n, k,
-                               ctypes.addressof(ab), pools.A.data_ptr(), max(1, ar), lda2,
-                               pools.B.data_ptr(), max(1, br), br * bc, ctypes.addressof(bb),
-                               pools.C.data_ptr(), max(1, m), m * n, N, variant, reps,
+                               ctypes.addressof(ab), pA.data_ptr(), max(1, ar), lda2,
+                               pB.data_ptr(), max(1, br), br * bc, ctypes.addressof(bb),
+                               pC.data_ptr(), max(1, m), m * n, N, variant, reps,
                                pools.flush.data_ptr(), pools.flush.numel(), s, ctypes.byref(ms))
     if st != 0:
         raise sbgemm.SbgemmError(st, "time_variant")
@@ -137,8 +151,9 @@ def time_nounif(pools, dtype, m, N, reps):
     torch = pools.torch
     es = ES[dtype]
     S = m * m
-    idx = torch.arange(N, device=pools.A.device, dtype=torch.int64) * (S * es)
-    Ap, Bp, Cp = idx + pools.A.data_ptr(), idx + pools.B.data_ptr(), idx + pools.C.data_ptr()
+    pA, pB, pC = pools.for_type(dtype)
+    idx = torch.arange(N, device=pA.device, dtype=torch.int64) * (S * es)
+    Ap, Bp, Cp = idx + pA.data_ptr(), idx + pB.data_ptr(), idx + pC.data_ptr()
     fn = lambda: sbgemm.gemm_multi_nounif(dtype, "N", "N", m, m, m, 1.0, Ap, m, Bp, m, 0.0, Cp,
                                           m, N)
     return time_fn(pools, fn, reps)
@@ -211,9 +226,10 @@ def _scalar_pair(dtype):
 def time_cublas(pools, dtype, m, n, k, N, reps):
     """cuBLAS strided batched (torch.bmm) on column-major N/N data, beta = 0."""
     torch = pools.torch
-    A = pools.as_dtype(pools.A, dtype)[:N * m * k].view(N, k, m)   # row-major view of A^T
-    B = pools.as_dtype(pools.B, dtype)[:N * k * n].view(N, n, k)   # row-major view of B^T
-    C = pools.as_dtype(pools.C, dtype)[:N * m * n].view(N, n, m)   # row-major view of C^T
+    pA, pB, pC = pools.for_type(dtype)
+    A = pools.as_dtype(pA, dtype)[:N * m * k].view(N, k, m)   # row-major view of A^T
+    B = pools.as_dtype(pB, dtype)[:N * k * n].view(N, n, k)   # row-major view of B^T
+    C = pools.as_dtype(pC, dtype)[:N * m * n].view(N, n, m)   # row-major view of C^T
     ts = []
     for _ in range(reps + 1):
         pools.evict()
@@ -454,8 +470,9 @@ def main(argv=None):
             for m in range(8, 17):
                 S = m * m
                 pools.evict()
-                sbgemm.gemm_multi_uniform(dtype, "N", "N", m, m, m, 1.0, pools.A.data_ptr(), m, S,
-                                          pools.B.data_ptr(), m, S, 0.0, pools.C.data_ptr(), m, S,
+                pA, pB, pC = pools.for_type(dtype)
+                sbgemm.gemm_multi_uniform(dtype, "N", "N", m, m, m, 1.0, pA.data_ptr(), m, S,
+                                          pB.data_ptr(), m, S, 0.0, pC.data_ptr(), m, S,
                                           100_000)
         torch.cuda.synchronize()
         want.discard("once")

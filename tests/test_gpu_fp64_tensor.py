@@ -81,6 +81,11 @@ def test_extreme_exponents_and_special_values():
     A[2, :m] = 0.0               # column 0 of pair 2's A
     A[3, 5] = np.nan
     B[4, 7] = np.inf
+    A[5, 0::m] = 0.0             # row 0 of pair 5's A
+    B[6, :m] = 0.0               # column 0 of pair 6's B
+    A[7] = 0.0                   # all of pair 7's A
+    A[8, 1::m] = np.ldexp(np.arange(1, m + 1), -1070)   # a subnormal row,
+    B[8] *= 2.0 ** 60                                    # products in the normal range
     got = H.run_gpu(b, 1.0, 0.0, variant=TC)
     ref_fma = H.run_gpu(b, 1.0, 0.0, variant=0)
     g, r = got.reshape(N, -1), ref_fma.reshape(N, -1)
