@@ -306,8 +306,9 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
  *   SBGEMM_SELECTOR_MODEL: the table's entry, else the installed cost
  *     model's choice, else the built-in rule.
  * Built-in rule: the tensor-core variant (7) for the 16-bit types at
- * m = n = k = 8 and 16 and for real fp64 at m = n = k >= 13; variant 2 for
- * complex64, and for fp32 with size_class <= 5; variant 0 otherwise.
+ * m = n = k = 8 and 16, and for real fp64 at m = n = k = 15, 16, at 13, 14
+ * with beta == 0 and at 16 x 8 x 16; variant 2 for complex64, and for fp32
+ * with size_class <= 5; variant 0 otherwise.
  * All of this is process-wide host state: set it before issuing work, not
  * concurrently with calls that read it.
  *
@@ -327,7 +328,7 @@ sbgemm_status sbgemm_set_choice(int type, int m, int n, int k, int ta, int tb,
 int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb,
                       int beta_zero, int size_class);
 /* The built-in rule's variant for the class (-1 for an invalid class). */
-int sbgemm_default_variant(int type, int m, int n, int k, int size_class);
+int sbgemm_default_variant(int type, int m, int n, int k, int beta_zero, int size_class);
 void sbgemm_clear_choices(void);
 /* The public variant index the calling thread's most recent fixed-size
  * call ran (-1 before any); for checking which kernel a selection reached. */

@@ -160,7 +160,7 @@ int evaluate_model_locked() {
         const float* y = &Y[(size_t)r * M.V];
         int best = 0;
         for (int v = 1; v < nv; ++v) if (y[v] < y[best]) best = v;
-        int dflt = default_variant(type, m, n, k, sc);
+        int dflt = default_variant(type, m, n, k, std::get<6>(key), sc);
         if (dflt >= nv) dflt = 0;
         // predicted times exp(y sd + mu): keep the default unless the best
         // is predicted faster by more than the trust margin
@@ -338,14 +338,21 @@ int variants_for(int type, int m, int n, int k) {
 //   complex64 at N = 1e5 and 1e6, and 5% less for fp32 at N = 1e5 (up to 20%
 //   per size), while fp32 at N = 1e6 measured the same total;
 // - the tensor-core kernel (digit-split products) for real fp64 at
-//   m = n = k >= 13: at N = 1e5 it took 410 / 409 / 406 / 378 us for
-//   m = 13 / 14 / 15 / 16 against 465 / 471 / 624 / 685 us on the fp64 FMA
-//   pipe (1.14-1.81x; below m = 13 the FMA kernels win, as the tensor-core
-//   kernel always computes a 16 x 16 x 16 product);
+//   m = n = k = 15, 16, at 13, 14 with beta == 0, and at 16 x 8 x 16: with
+//   alpha = 1.5 at N = 1e5 it took 421 / 427 / 426 / 398 us for
+//   m = 13 / 14 / 15 / 16 against 496 / 508 / 648 / 739 us on the fp64 FMA
+//   pipe with beta = 0 (1.18-1.86x), 571 / 588 / 589 / 509 us against
+//   551 / 557 / 733 / 791 us with beta = -0.5 (C read and updated in fp64),
+//   and 289 us against 404 us for 16 x 8 x 16 (op(A) = T, beta = 1); below
+//   m = 13 and on the other FEM shapes the FMA kernels win, as the
+//   tensor-core kernel always computes a 16 x 16 x 16 product;
 // - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
 //   no difference; the 16-bit CUDA-core kernels were mixed).
-int default_variant(int type, int m, int n, int k, int sc) {
-    if (type == SBGEMM_TYPE_D && m == n && n == k && m >= 13) return kMmaVariant;
+int default_variant(int type, int m, int n, int k, int bz, int sc) {
+    if (type == SBGEMM_TYPE_D) {
+        if (m == n && n == k && (m >= 15 || (m >= 13 && bz))) return kMmaVariant;
+        if (m == 16 && n == 8 && k == 16) return kMmaVariant;
+    }
     if (has_mma_variant(type, m, n, k) && type != SBGEMM_TYPE_D && m != 12) return kMmaVariant;
     if (!has_specialized(0, m, n, k)) return 0;
     if (type == SBGEMM_TYPE_C || (type == SBGEMM_TYPE_S && sc <= 5)) return 2;
@@ -364,7 +371,7 @@ int select_variant(int type, int m, int n, int k, int ta, int tb, int bz, int sc
         const int v = model_choice(type, m, n, k, ta, tb, bz, sc);
         if (v >= 0 && v < nv) return v;
     }
-    return default_variant(type, m, n, k, sc);
+    return default_variant(type, m, n, k, bz, sc);
 }
 
 void note_variant(int v) { t_last_variant = v; }
@@ -392,10 +399,10 @@ int sbgemm_get_choice(int type, int m, int n, int k, int ta, int tb, int beta_ze
     return sbg::select_variant(type, m, n, k, ta ? 1 : 0, tb ? 1 : 0, beta_zero ? 1 : 0, size_class);
 }
 
-int sbgemm_default_variant(int type, int m, int n, int k, int size_class) {
+int sbgemm_default_variant(int type, int m, int n, int k, int beta_zero, int size_class) {
     if (type < SBGEMM_TYPE_S || type > SBGEMM_TYPE_B || size_class < 0 || size_class > 7) return -1;
     if (sbg::variants_for(type, m, n, k) == 0) return -1;
-    return sbg::default_variant(type, m, n, k, size_class);
+    return sbg::default_variant(type, m, n, k, beta_zero ? 1 : 0, size_class);
 }
 
 void sbgemm_clear_choices(void) {

@@ -16,7 +16,7 @@ int size_class(int batch);
 // number of public variants of a (type, m, n, k) problem; 0 when invalid
 int variants_for(int type, int m, int n, int k);
 // the built-in choice without a table entry or cost model
-int default_variant(int type, int m, int n, int k, int sc);
+int default_variant(int type, int m, int n, int k, int beta_zero, int sc);
 // the choice under the current selector mode
 int select_variant(int type, int m, int n, int k, int ta, int tb, int beta_zero, int sc);
 // remember the variant the calling thread's latest fixed-size call used

@@ -57,7 +57,7 @@ SIGNATURES = {
     "sbgemm_set_choice": (_i, [_i] * 9),
     "sbgemm_get_choice": (_i, [_i] * 8),
     "sbgemm_clear_choices": (None, []),
-    "sbgemm_default_variant": (_i, [_i] * 5),
+    "sbgemm_default_variant": (_i, [_i] * 6),
     "sbgemm_last_variant": (_i, []),
     "sbgemm_save_table": (_i, [ctypes.c_char_p]),
     "sbgemm_load_table": (_i, [ctypes.c_char_p]),
@@ -270,8 +270,8 @@ def clear_choices() -> None:
     lib().sbgemm_clear_choices()
 
 
-def default_variant(dtype, m, n, k, size_class) -> int:
-    return lib().sbgemm_default_variant(TYPE_CODES[dtype], m, n, k, size_class)
+def default_variant(dtype, m, n, k, beta_zero, size_class) -> int:
+    return lib().sbgemm_default_variant(TYPE_CODES[dtype], m, n, k, int(beta_zero), size_class)
 
 
 def last_variant() -> int:

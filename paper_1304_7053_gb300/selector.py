@@ -385,7 +385,7 @@ def default_choices(classes) -> np.ndarray:
     """The library's built-in choice for each class (``sbgemm_default_variant``:
     the tensor-core variant of the 16-bit types at m = n = k = 8, 16; variant
     2 for complex64 and for fp32 below 1e6 pairs; variant 0 otherwise)."""
-    return np.array([sbgemm.default_variant(c[0], c[1], c[2], c[3], size_class(c[8]))
+    return np.array([sbgemm.default_variant(c[0], c[1], c[2], c[3], c[7], size_class(c[8]))
                      for c in classes], dtype=np.int64)
 
 

@@ -27,7 +27,9 @@ workload; ``vbatch`` (only when named) compares the variable-size plan with
 cublasSgemmGroupedBatched on the fp32 mixed-size batch; ``once`` (only when
 named) makes one untimed call per type and
 size (fp32 and fp64, m = 8..16, N = 1e5, op N/N, alpha = 1, beta = 0, L2
-evicted before each): the launches a kernel-level profile reads.
+evicted before each): the launches a kernel-level profile reads.  ``fp64tc``
+(only when named) times real fp64 on the fp64 FMA kernel (variant 0) and on
+the tensor-core kernel (variant 7).
 """
 from __future__ import annotations
 
@@ -549,6 +551,21 @@ def main(argv=None):
                 r["streamed_a_ms"] = round(ms_u, 5)
                 r["speedup_vs_streamed_a"] = round(ms_u / ms_s, 2)
                 emit(r, "shared_a")
+    # real fp64: the fp64 FMA kernel (variant 0) against the tensor-core
+    # kernel (variant 7), square N/N and the FEM shapes, alpha = 1.5
+    if "fp64tc" in want:
+        for N in (100_000, 1_000_000):
+            for (m, n, k, ta, beta) in [(s_, s_, s_, "N", b_) for s_ in sizes for b_ in (0.0, -0.5)] + \
+                    [(4, 16, 4, "T", 1.0), (9, 16, 9, "T", 1.0), (16, 8, 16, "T", 1.0),
+                     (3, 9, 3, "T", 1.0), (16, 16, 1, "T", 1.0)]:
+                if N == 1_000_000 and (m != n or m not in (8, 12, 13, 14, 15, 16)):
+                    continue
+                ms0 = time_ours(pools, "d", ta, "N", m, n, k, N, 1.5, beta, args.reps, variant=0)
+                ms7 = time_ours(pools, "d", ta, "N", m, n, k, N, 1.5, beta, args.reps, variant=7)
+                r = row("d", ta, "N", m, n, k, N, beta, ms7)
+                r["fma_ms"] = round(ms0, 5)
+                r["tensor_over_fma_speedup"] = round(ms0 / ms7, 2)
+                emit(r, "fp64tc")
     # 16-bit storage
     if "16bit" in want:
         for dtype in ("h", "b"):

@@ -112,7 +112,8 @@ def test_variant_table_host_logic():
     assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 6) == 0
     assert sbgemm.get_choice("c", 10, 10, 10, 0, 0, 1, 6) == 2
     assert sbgemm.get_choice("d", 10, 10, 10, 0, 0, 1, 5) == 0
-    assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 7
+    assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 1, 5) == 7
+    assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 0
     assert sbgemm.get_choice("d", 12, 12, 12, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("h", 16, 16, 16, 0, 0, 1, 6) == 7

@@ -71,7 +71,7 @@ def test_fresh_process_applies_table_and_cost_model(tmp_path):
     assert out["choice_m10"] == 4 and out["ran_m10"] == 4          # the model's choice
     assert out["choice_m12"] == 3 and out["ran_m12"] == 3          # the table wins
     assert out["choice_generic"] == 0                                # one variant only
-    assert out["ran_m10_table_mode"] == sbgemm.default_variant("d", 10, 10, 10, 3)
+    assert out["ran_m10_table_mode"] == sbgemm.default_variant("d", 10, 10, 10, 1, 3)
 
 
 def test_library_evaluation_matches_trainer():
@@ -100,7 +100,7 @@ def test_library_evaluation_matches_trainer():
                 for ta, tb, bz, sc in ((0, 0, 1, 3), (1, 0, 0, 5), (0, 1, 1, 6)):
                     f = selector.features(dt, m, nn, k, ta, tb, 0, bz, 10 ** (sc + 0.5))[None, :]
                     nvalid = np.array([sbgemm.num_variants(dt, m, nn, k)])
-                    dflt = np.array([sbgemm.default_variant(dt, m, nn, k, sc)])
+                    dflt = np.array([sbgemm.default_variant(dt, m, nn, k, bz, sc)])
                     want = int(net.choose(f, nvalid, margin, dflt)[0])
                     got = sbgemm.get_choice(dt, m, nn, k, ta, tb, bz, sc)
                     if got != want:

@@ -43,7 +43,7 @@ def test_table_file_round_trip(tmp_path):
     assert lines[0] == "sbgemm-table 1" and lines[1].startswith("device ")
     sbgemm.clear_choices()
     for e in ENTRIES:
-        assert L.sbgemm_get_choice(*e[:8]) == L.sbgemm_default_variant(e[0], e[1], e[2], e[3], e[7])
+        assert L.sbgemm_get_choice(*e[:8]) == L.sbgemm_default_variant(e[0], e[1], e[2], e[3], e[6], e[7])
     sbgemm.load_table(p)
     for e in ENTRIES:
         assert L.sbgemm_get_choice(*e[:8]) == e[8]
@@ -68,7 +68,7 @@ def test_malformed_table_is_rejected_and_adds_nothing(tmp_path, body):
                        body.replace("sbgemm-table 1\n", "sbgemm-table 1\n3 8 8 8 0 0 0 5 5\n"))
     assert sbgemm.lib().sbgemm_load_table(p.encode()) == -9
     assert sbgemm.lib().sbgemm_get_choice(Z, 8, 8, 8, 0, 0, 0, 5) == \
-        sbgemm.lib().sbgemm_default_variant(Z, 8, 8, 8, 5)
+        sbgemm.lib().sbgemm_default_variant(Z, 8, 8, 8, 0, 5)
     assert sbgemm.lib().sbgemm_load_table(str(tmp_path / "missing.txt").encode()) == -9
 
 
@@ -77,20 +77,27 @@ def test_selector_modes():
     assert L.sbgemm_set_choice(S, 10, 10, 10, 0, 0, 1, 5, 4) == 0
     assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == 4
     sbgemm.set_selector(sbgemm.SELECTOR_DEFAULT)
-    assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == L.sbgemm_default_variant(S, 10, 10, 10, 5)
+    assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == L.sbgemm_default_variant(S, 10, 10, 10, 1, 5)
     assert sbgemm.get_selector()[0] == sbgemm.SELECTOR_DEFAULT
     sbgemm.set_selector(sbgemm.SELECTOR_TABLE)
     assert L.sbgemm_get_choice(S, 10, 10, 10, 0, 0, 1, 5) == 4
     assert L.sbgemm_set_selector(7) == -5
     # the built-in rule itself
-    assert L.sbgemm_default_variant(H, 16, 16, 16, 6) == 7
-    assert L.sbgemm_default_variant(H, 12, 12, 12, 6) == 0
-    assert L.sbgemm_default_variant(C, 10, 10, 10, 6) == 2
-    assert L.sbgemm_default_variant(S, 10, 10, 10, 5) == 2
-    assert L.sbgemm_default_variant(S, 10, 10, 10, 6) == 0
-    assert L.sbgemm_default_variant(D, 10, 10, 10, 5) == 0
-    assert L.sbgemm_default_variant(S, 7, 3, 11, 5) == 0
-    assert L.sbgemm_default_variant(S, 17, 3, 11, 5) == -1
+    assert L.sbgemm_default_variant(H, 16, 16, 16, 1, 6) == 7
+    assert L.sbgemm_default_variant(H, 12, 12, 12, 1, 6) == 0
+    assert L.sbgemm_default_variant(C, 10, 10, 10, 1, 6) == 2
+    assert L.sbgemm_default_variant(S, 10, 10, 10, 1, 5) == 2
+    assert L.sbgemm_default_variant(S, 10, 10, 10, 1, 6) == 0
+    assert L.sbgemm_default_variant(D, 10, 10, 10, 1, 5) == 0
+    assert L.sbgemm_default_variant(S, 7, 3, 11, 1, 5) == 0
+    assert L.sbgemm_default_variant(S, 17, 3, 11, 1, 5) == -1
+    # real fp64 on the tensor cores: m = n = k >= 15, 13 and 14 with beta == 0, 16 x 8 x 16
+    assert L.sbgemm_default_variant(D, 16, 16, 16, 0, 5) == 7
+    assert L.sbgemm_default_variant(D, 13, 13, 13, 1, 5) == 7
+    assert L.sbgemm_default_variant(D, 13, 13, 13, 0, 5) == 0
+    assert L.sbgemm_default_variant(D, 12, 12, 12, 1, 5) == 0
+    assert L.sbgemm_default_variant(D, 16, 8, 16, 0, 6) == 7
+    assert L.sbgemm_default_variant(D, 9, 16, 9, 0, 6) == 0
 
 
 def _params(seed=3):
@@ -157,7 +164,7 @@ def test_environment_settings_in_a_fresh_process(tmp_path):
         assert r.returncode == 0, r.stderr
         return json.loads(r.stdout.strip().splitlines()[-1])
 
-    dflt = L.sbgemm_default_variant(S, 10, 10, 10, 5)
+    dflt = L.sbgemm_default_variant(S, 10, 10, 10, 1, 5)
     assert run() == [[1, 0], dflt]
     assert run(SBGEMM_TABLE=p) == [[1, 0], 4]
     assert run(SBGEMM_TABLE=p, SBGEMM_SELECTOR="default") == [[0, 0], dflt]
