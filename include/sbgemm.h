@@ -275,7 +275,8 @@ sbgemm_status sbgemm_gemm_multi_nounif(int type, char transa, char transb, int m
  * (for fp64: operands split into exact 8-bit digits whose products run on
  * the binary16 MMA path, recombined exactly; entries whose accuracy the
  * split cannot guarantee are recomputed with fp64 FMAs).  Other shapes have
- * the generic kernel only. */
+ * the generic kernel as variant 0 and, for real fp64 only, the same
+ * tensor-core kernel as variant 1. */
 int sbgemm_num_variants(int type, int m, int n, int k);
 
 /* Human-readable description of a variant (static storage, never NULL). */
@@ -362,10 +363,14 @@ sbgemm_status sbgemm_get_selector(int* mode, int* env_status);
  * order; opA and opB transposed; conjugation (0); beta == 0; a flag for
  * shapes with specialised kernels; (mnk)^(1/3) / 16), H hidden units and
  * V outputs, output v the standardised log-time of variant v: predicted
- * time = exp(y_v * log_time_std + log_time_mean).  For each class with more
- * than one variant the model's choice is the valid variant with the
- * smallest prediction if that is below (1 - margin) times the prediction
- * of the built-in rule's variant, else the built-in rule's variant.
+ * time = exp(y_v * log_time_std + log_time_mean) (only ratios between the
+ * variants of one class are used, so the outputs may be log-times relative
+ * to any per-class reference).  For each class with more than one variant
+ * the model's choice is the valid variant with the smallest prediction if
+ * that is below (1 - margins[type]) times the prediction of the built-in
+ * rule's variant, else the built-in rule's variant: `margins` holds one
+ * trust margin per storage type, indexed by type code (SBGEMM_TYPE_S ..
+ * SBGEMM_TYPE_B), each in [0, 1]; 1 keeps the built-in rule for that type.
  * sbgemm_set_cost_model copies `params` (host array of
  * sbgemm_mlp_param_count(F, H, V) floats) and replaces any installed model.
  * The choices of every class are evaluated at once, on the current GPU,
@@ -374,15 +379,19 @@ sbgemm_status sbgemm_get_selector(int* mode, int* env_status);
  * mode becomes MODEL, or at the first call that needs them when the model
  * and mode come from the environment; make that first call outside any
  * stream capture.  F must be 16, 1 <= H <= 4096, 1 <= V <= 64,
- * log_time_std > 0, 0 <= margin < 1 (else SBGEMM_ERR_INVALID_VALUE).
+ * log_time_std > 0, every margin in [0, 1] (else SBGEMM_ERR_INVALID_VALUE);
+ * params or margins NULL: SBGEMM_ERR_NULL_POINTER.
  */
 sbgemm_status sbgemm_set_cost_model(int F, int H, int V, const float* params,
-                                    double log_time_mean, double log_time_std, double margin);
+                                    double log_time_mean, double log_time_std,
+                                    const double* margins);
 /*
- * Cost-model files (text, version 1): "sbgemm-cost-model 1", "device
+ * Cost-model files (text, version 2): "sbgemm-cost-model 2", "device
  * <name>" (the GPU it was trained on), "features F hidden H outputs V",
- * "log_time_mean mu log_time_std sd margin m", "params n", then the n
- * parameters (9 significant digits, exact for fp32).  Loading installs the
+ * "log_time_mean mu log_time_std sd", "margins m_S m_D m_C m_Z m_H m_B",
+ * "params n", then the n parameters (9 significant digits, exact for
+ * fp32).  Version 1 files (one "margin m" for every type after the
+ * log-time line) still load.  Loading installs the
  * model as sbgemm_set_cost_model does; SBGEMM_ERR_IO for an unreadable or
  * malformed file; SBGEMM_ERR_INVALID_VALUE from sbgemm_save_cost_model when
  * no model is installed.

@@ -85,10 +85,13 @@ bool host_scalar_zero(int type, const void* p) {
     }
 }
 
-// Map a public variant index to the internal one (generic kernel index =
-// kNumPipeVariants).
-int internal_variant(int m, int n, int k, int v) {
-    return has_specialized(0, m, n, k) ? v : kNumPipeVariants;
+// Map a public variant index to the internal one.  Shapes with specialised
+// kernels use the internal index as is; the other shapes have the generic
+// kernel (internal kNumPipeVariants) as variant 0 and, for real fp64, the
+// tensor-core kernel (internal kMmaVariant) as variant 1.
+int internal_variant(int type, int m, int n, int k, int v) {
+    if (has_specialized(0, m, n, k)) return v;
+    return type == SBGEMM_TYPE_D && v == 1 ? kMmaVariant : kNumPipeVariants;
 }
 
 sbgemm_status run_typed(const Req& r) {
@@ -170,7 +173,7 @@ sbgemm_status gemm_uniform(int type, char transa, char transb, int m, int n, int
                                  size_class(batch));
     }
     note_variant(variant);
-    r.variant = internal_variant(m, n, k, variant);
+    r.variant = internal_variant(type, m, n, k, variant);
     return run_typed(r);
 }
 
@@ -219,7 +222,7 @@ sbgemm_status gemm_nounif(int type, char transa, char transb, int m, int n, int 
                                        scalar_mode == SBGEMM_SCALARS_HOST ? r.beta_zero : 0,
                                        size_class(batch));
     note_variant(variant);
-    r.variant = internal_variant(m, n, k, variant);
+    r.variant = internal_variant(type, m, n, k, variant);
     return run_typed(r);
 }
 
@@ -310,7 +313,7 @@ const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
         "tensor-core: mma.sync for 16-bit N/N flat; 8-bit digit products for fp64; else variant 0"};
     const int nv = sbgemm_num_variants(type, m, n, k);
     if (variant < 0 || variant >= nv) return "invalid";
-    return names[sbg::internal_variant(m, n, k, variant)];
+    return names[sbg::internal_variant(type, m, n, k, variant)];
 }
 
 sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char transb,

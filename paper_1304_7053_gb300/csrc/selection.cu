@@ -7,6 +7,7 @@
 // consultation under the default mode: a table entry, else the built-in
 // default rule; under the model mode a table entry, else the cost model's
 // choice, else the default rule.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -40,7 +41,8 @@ struct CostModel {
     bool present = false;
     int F = 0, H = 0, V = 0;
     std::vector<float> params;
-    double mu = 0.0, sd = 1.0, margin = 0.0;
+    double mu = 0.0, sd = 1.0;
+    double margin[6] = {0, 0, 0, 0, 0, 0};   // trust margin per storage type
     std::string device;
     bool evaluated = false;        // choices below are current
     int eval_status = 0;           // error of the last evaluation (0: none)
@@ -99,8 +101,8 @@ void class_features(int type, int m, int n, int k, int ta, int tb, int bz, int s
 }
 
 // Evaluate the network once for every class that has a choice (the shapes
-// with specialised kernels), on the GPU with this library's forward kernel,
-// and keep the chosen variant per class.  Caller holds g_model_mu.
+// with specialised kernels, and every real fp64 shape), on the GPU with this
+// library's forward kernel, and keep the chosen variant per class.  Caller holds g_model_mu.
 int evaluate_model_locked() {
     CostModel& M = g_model;
     M.choice.clear();
@@ -121,26 +123,34 @@ int evaluate_model_locked() {
                                     class_features(type, m, n, k, ta, tb, bz, sc, &X[X.size() - 16]);
                                 }
                 }
+    // forward in chunks of rows, so the work buffer stays small (about 16 MB)
+    // whatever the number of classes
     const int rows = (int)keys.size();
+    const int chunk = 16384;
     const size_t np = M.params.size();
     std::vector<float> Y((size_t)rows * M.V);
     float *dp = nullptr, *dx = nullptr, *dy = nullptr, *dw = nullptr;
     cudaStream_t s = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&dp, np * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&dx, X.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&dy, Y.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&dw, (size_t)4 * rows * M.H * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dx, (size_t)chunk * 16 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dy, (size_t)chunk * M.V * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dw, (size_t)4 * chunk * M.H * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dp, M.params.data(), np * sizeof(float), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dx, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, s);
     int st = e == cudaSuccess ? 0 : (int)e;
-    if (st == 0) st = sbgemm_mlp_forward(M.F, M.H, M.V, dp, dx, rows, dy, dw, s);
-    if (st == 0) {
-        e = cudaMemcpyAsync(Y.data(), dy, Y.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int r0 = 0; st == 0 && r0 < rows; r0 += chunk) {
+        const int nr = std::min(chunk, rows - r0);
+        e = cudaMemcpyAsync(dx, &X[(size_t)r0 * 16], (size_t)nr * 16 * sizeof(float),
+                            cudaMemcpyHostToDevice, s);
         st = e == cudaSuccess ? 0 : (int)e;
+        if (st == 0) st = sbgemm_mlp_forward(M.F, M.H, M.V, dp, dx, nr, dy, dw, s);
+        if (st == 0) {
+            e = cudaMemcpyAsync(&Y[(size_t)r0 * M.V], dy, (size_t)nr * M.V * sizeof(float),
+                                cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            st = e == cudaSuccess ? 0 : (int)e;
+        }
     }
     if (dp) cudaFree(dp);
     if (dx) cudaFree(dx);
@@ -166,7 +176,7 @@ int evaluate_model_locked() {
         // is predicted faster by more than the trust margin
         const double tb_ = std::exp((double)y[best] * M.sd + M.mu);
         const double td_ = std::exp((double)y[dflt] * M.sd + M.mu);
-        M.choice[key] = tb_ < td_ * (1.0 - M.margin) ? best : dflt;
+        M.choice[key] = tb_ < td_ * (1.0 - M.margin[type]) ? best : dflt;
     }
     M.evaluated = true;
     M.eval_status = 0;
@@ -225,16 +235,23 @@ int read_model_file(const char* path, CostModel* M) {
     long long np = 0;
     do {
         if (!std::fgets(buf, sizeof buf, f) || std::sscanf(buf, "sbgemm-cost-model %d", &ver) != 1 ||
-            ver != 1)
+            (ver != 1 && ver != 2))
             break;
         if (!std::fgets(buf, sizeof buf, f) || std::strncmp(buf, "device ", 7) != 0) break;
         M->device.assign(buf + 7);
         while (!M->device.empty() && (M->device.back() == '\n' || M->device.back() == '\r'))
             M->device.pop_back();
         if (std::fscanf(f, " features %d hidden %d outputs %d", &M->F, &M->H, &M->V) != 3) break;
-        if (std::fscanf(f, " log_time_mean %lf log_time_std %lf margin %lf", &M->mu, &M->sd,
-                        &M->margin) != 3)
-            break;
+        if (std::fscanf(f, " log_time_mean %lf log_time_std %lf", &M->mu, &M->sd) != 2) break;
+        if (ver == 1) {          // one margin for every storage type
+            if (std::fscanf(f, " margin %lf", &M->margin[0]) != 1) break;
+            for (int t = 1; t < 6; ++t) M->margin[t] = M->margin[0];
+        } else {
+            double* g = M->margin;
+            if (std::fscanf(f, " margins %lf %lf %lf %lf %lf %lf", g, g + 1, g + 2, g + 3, g + 4,
+                            g + 5) != 6)
+                break;
+        }
         if (std::fscanf(f, " params %lld", &np) != 1) break;
         if (np != sbgemm_mlp_param_count(M->F, M->H, M->V) || np <= 0) break;
         M->params.resize((size_t)np);
@@ -250,9 +267,14 @@ int read_model_file(const char* path, CostModel* M) {
     return st;
 }
 
-bool model_args_ok(int F, int H, int V, double sd, double margin) {
-    return F == 16 && H >= 1 && H <= 4096 && V >= 1 && V <= 64 && std::isfinite(sd) && sd > 0 &&
-           std::isfinite(margin) && margin >= 0 && margin < 1;
+// margins: one per storage type, 0 <= margin <= 1 (1: the built-in rule's
+// variant is always kept for that type)
+bool model_args_ok(int F, int H, int V, double sd, const double* margin) {
+    if (!(F == 16 && H >= 1 && H <= 4096 && V >= 1 && V <= 64 && std::isfinite(sd) && sd > 0))
+        return false;
+    for (int t = 0; t < 6; ++t)
+        if (!std::isfinite(margin[t]) || margin[t] < 0 || margin[t] > 1) return false;
+    return true;
 }
 
 int install_model(CostModel&& M) {
@@ -323,7 +345,9 @@ int size_class(int batch) {
 
 int variants_for(int type, int m, int n, int k) {
     if (m < 1 || n < 1 || k < 1 || m > 16 || n > 16 || k > 16) return 0;
-    if (!has_specialized(0, m, n, k)) return 1;
+    // shapes without specialised kernels: the generic kernel, and for real
+    // fp64 also the tensor-core kernel (public variant 1)
+    if (!has_specialized(0, m, n, k)) return type == SBGEMM_TYPE_D ? 2 : 1;
     return has_mma_variant(type, m, n, k) ? kMmaVariant + 1 : kNumPipeVariants + 1;
 }
 
@@ -346,10 +370,17 @@ int variants_for(int type, int m, int n, int k) {
 //   and 289 us against 404 us for 16 x 8 x 16 (op(A) = T, beta = 1); below
 //   m = 13 and on the other FEM shapes the FMA kernels win, as the
 //   tensor-core kernel always computes a 16 x 16 x 16 product;
+// - for real fp64 shapes without specialised kernels, the tensor-core
+//   kernel (public variant 1) when m n k >= 1320 with beta == 0 or >= 1792
+//   otherwise: over the 334 such shapes with m, n, k in {4, 8, 11, 13, 14,
+//   15, 16}, op N/N, N = 1e5, this rule took 101.4 / 123.7 ms in total
+//   (beta == 0 / beta = -0.5) against 100.6 / 121.0 ms for the best
+//   variant of each shape and 129.5 / 135.3 ms for the generic kernel alone;
 // - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
 //   no difference; the 16-bit CUDA-core kernels were mixed).
 int default_variant(int type, int m, int n, int k, int bz, int sc) {
     if (type == SBGEMM_TYPE_D) {
+        if (!has_specialized(0, m, n, k)) return m * n * k >= (bz ? 1320 : 1792) ? 1 : 0;
         if (m == n && n == k && (m >= 15 || (m >= 13 && bz))) return kMmaVariant;
         if (m == 16 && n == 8 && k == 16) return kMmaVariant;
     }
@@ -478,10 +509,10 @@ sbgemm_status sbgemm_get_selector(int* mode, int* env_status) {
 }
 
 sbgemm_status sbgemm_set_cost_model(int F, int H, int V, const float* params, double log_time_mean,
-                                    double log_time_std, double margin) {
+                                    double log_time_std, const double* margins) {
     sbg::init_from_env();
-    if (!params) return SBGEMM_ERR_NULL_POINTER;
-    if (!sbg::model_args_ok(F, H, V, log_time_std, margin) || !std::isfinite(log_time_mean))
+    if (!params || !margins) return SBGEMM_ERR_NULL_POINTER;
+    if (!sbg::model_args_ok(F, H, V, log_time_std, margins) || !std::isfinite(log_time_mean))
         return SBGEMM_ERR_INVALID_VALUE;
     const long long np = sbgemm_mlp_param_count(F, H, V);
     sbg::CostModel M;
@@ -489,7 +520,8 @@ sbgemm_status sbgemm_set_cost_model(int F, int H, int V, const float* params, do
     M.params.assign(params, params + np);
     for (float x : M.params)
         if (!std::isfinite(x)) return SBGEMM_ERR_INVALID_VALUE;
-    M.mu = log_time_mean; M.sd = log_time_std; M.margin = margin;
+    M.mu = log_time_mean; M.sd = log_time_std;
+    for (int t = 0; t < 6; ++t) M.margin[t] = margins[t];
     M.device = sbg::device_name();
     return sbg::install_model(std::move(M));
 }
@@ -503,15 +535,19 @@ sbgemm_status sbgemm_save_cost_model(const char* path) {
         if (!sbg::g_model.present) return SBGEMM_ERR_INVALID_VALUE;
         M.F = sbg::g_model.F; M.H = sbg::g_model.H; M.V = sbg::g_model.V;
         M.params = sbg::g_model.params;
-        M.mu = sbg::g_model.mu; M.sd = sbg::g_model.sd; M.margin = sbg::g_model.margin;
+        M.mu = sbg::g_model.mu; M.sd = sbg::g_model.sd;
+        for (int t = 0; t < 6; ++t) M.margin[t] = sbg::g_model.margin[t];
         M.device = sbg::g_model.device;
     }
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
     if (!f) return SBGEMM_ERR_IO;
-    std::fprintf(f, "sbgemm-cost-model 1\ndevice %s\n", M.device.c_str());
+    std::fprintf(f, "sbgemm-cost-model 2\ndevice %s\n", M.device.c_str());
     std::fprintf(f, "features %d hidden %d outputs %d\n", M.F, M.H, M.V);
-    std::fprintf(f, "log_time_mean %.17g log_time_std %.17g margin %.17g\n", M.mu, M.sd, M.margin);
+    std::fprintf(f, "log_time_mean %.17g log_time_std %.17g\n", M.mu, M.sd);
+    std::fprintf(f, "margins");
+    for (int t = 0; t < 6; ++t) std::fprintf(f, " %.17g", M.margin[t]);
+    std::fprintf(f, "\n");
     std::fprintf(f, "params %lld\n", (long long)M.params.size());
     for (size_t i = 0; i < M.params.size(); ++i)
         std::fprintf(f, "%.9g%c", M.params[i], (i % 8 == 7 || i + 1 == M.params.size()) ? '\n' : ' ');

@@ -63,8 +63,7 @@ SIGNATURES = {
     "sbgemm_load_table": (_i, [ctypes.c_char_p]),
     "sbgemm_set_selector": (_i, [_i]),
     "sbgemm_get_selector": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_i)]),
-    "sbgemm_set_cost_model": (_i, [_i, _i, _i, _vp, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double]),
+    "sbgemm_set_cost_model": (_i, [_i, _i, _i, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "sbgemm_save_cost_model": (_i, [ctypes.c_char_p]),
     "sbgemm_load_cost_model": (_i, [ctypes.c_char_p]),
     "sbgemm_tune": (_i, [_i] + _UNIFORM + [_i, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i),
@@ -308,13 +307,29 @@ def load_table(path: str) -> None:
         raise SbgemmError(st, "load_table")
 
 
+def margin_array(margins):
+    """Per-storage-type trust margins in type-code order: a number (every
+    type), a mapping from dtype letter to margin (missing types: 0), or a
+    sequence of six."""
+    if isinstance(margins, dict):
+        return [float(margins.get(d, 0.0)) for d in "sdczhb"]
+    if isinstance(margins, (int, float)):
+        return [float(margins)] * 6
+    out = [float(x) for x in margins]
+    if len(out) != 6:
+        raise ValueError("six margins expected, one per storage type")
+    return out
+
+
 def set_cost_model(F: int, H: int, V: int, params, log_time_mean: float, log_time_std: float,
-                   margin: float) -> None:
-    """Install a cost model from a host float32 numpy array of parameters."""
+                   margins) -> None:
+    """Install a cost model from a host float32 numpy array of parameters;
+    ``margins`` as ``margin_array`` takes them."""
     import numpy as np
     p = np.ascontiguousarray(params, dtype=np.float32)
+    mg = np.ascontiguousarray(margin_array(margins), dtype=np.float64)
     st = lib().sbgemm_set_cost_model(F, H, V, p.ctypes.data, float(log_time_mean),
-                                     float(log_time_std), float(margin))
+                                     float(log_time_std), mg.ctypes.data)
     if st != 0:
         raise SbgemmError(st, "set_cost_model")
 

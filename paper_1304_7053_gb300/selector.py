@@ -13,10 +13,15 @@ on the batch at hand: the bucketing window of a variable-size plan
 (``tune_grouped``).
 
 The learned selector is a 3-layer perceptron (``sbgemm_mlp_*`` kernels,
-fp32) that maps problem features to one predicted log-time per variant.  It
-is trained on the database with the library's own forward, backward and Adam
-kernels; at selection time the variant with the smallest prediction among
-the valid ones wins and is installed in the library's selection table.
+fp32) that maps problem features to one predicted log-time per variant,
+relative to the class's mean variant.  It is trained on the database with
+the library's own forward, backward and Adam kernels.  At selection time
+the valid variant with the smallest prediction wins if it is predicted to
+beat the library's built-in rule by more than a trust margin; the margin is
+picked per storage type on out-of-fold predictions (networks that did not
+see the classes they are judged on), so the network is switched off for a
+type where it does not beat the rule.  The choices go to the library as a
+selection table or as the network itself (the MODEL selector mode).
 """
 from __future__ import annotations
 
@@ -35,10 +40,9 @@ NVAR = 9          # variants of specialised shapes; generic shapes have fewer
 HIDDEN = 64
 # L2 penalty on the network's parameters.  Without it the network fits the
 # few hundred training classes almost exactly and generalises worse than the
-# library's default choice (held-out mean regret 3.0% against 2.5%); with
-# 5e-3 it reached 1.9% on the held-out classes and 1.6% against 2.05% with
-# the training and held-out sets swapped, with the total time of its choices
-# at or below the default's in both.
+# library's built-in rule (held-out mean regret 3.0% against 2.5%, with
+# absolute log-time targets); with 5e-3 it reached 1.9% on the held-out
+# classes and 1.6% against 2.05% with the training and held-out sets swapped.
 L2_PENALTY = 5e-3
 TORCH_DT = {"s": "float32", "d": "float64", "c": "float32", "z": "float64",
             "h": "float16", "b": "bfloat16"}
@@ -111,12 +115,15 @@ class Tuner:
         self.flush = torch.empty(flush_bytes, dtype=torch.uint8, device=self.dev)
         self.stream = torch.cuda.current_stream(self.dev)
         self.name = device_name()
-        # one set of operand buffers for every class (uniform[-1, 1) fp32
-        # values; timing does not depend on the values)
-        g = torch.Generator(device=self.dev)
-        g.manual_seed(3)
-        n = (max_bytes + 3) // 4
-        self.pool = [torch.rand(n, device=self.dev, generator=g) * 2 - 1 for _ in range(3)]
+        # one set of operand buffers for every class, refilled with
+        # uniform[-1, 1) values of the element width the class reads
+        # (``TORCH_DT``).  The values matter: the fp64 tensor-core kernel
+        # recomputes with fp64 FMAs every entry whose accuracy its digit
+        # split cannot guarantee, which fp32 bit patterns read as doubles
+        # (wildly spread exponents) trigger often.
+        n = (max_bytes + 7) // 8 * 8
+        self.pool = [torch.empty(n, dtype=torch.uint8, device=self.dev) for _ in range(3)]
+        self._fill = None
         self.max_bytes = max_bytes
 
     def _buffers(self, dtype, m, n, k, ta, tb, N):
@@ -126,6 +133,14 @@ class Tuner:
         need = es * N * max(ar * ac, br * bc, m * n)
         if need > self.max_bytes:
             raise ValueError("problem class larger than the tuner's buffers")
+        fam = TORCH_DT[dtype]
+        if self._fill != fam:
+            torch = self.torch
+            g = torch.Generator(device=self.dev)
+            g.manual_seed(3 + sorted(set(TORCH_DT.values())).index(fam))
+            for t in self.pool:
+                t.view(getattr(torch, fam)).uniform_(-1.0, 1.0, generator=g)
+            self._fill = fam
         return tuple(self.pool), (max(1, ar), ar * ac, max(1, br), br * bc, max(1, m), m * n)
 
     def time_class(self, dtype, m, n, k, ta, tb, conj, beta0, N) -> list[float]:
@@ -326,16 +341,25 @@ class CostModel:
     # -------- training on timing data
     def fit(self, feats: np.ndarray, times: np.ndarray, steps=2000, lr=3e-3, l2=L2_PENALTY):
         """feats: (B, F); times: (B, V) ms with NaN where a variant was not
-        timed.  Targets are standardised log-times; ``l2`` penalises the
+        timed.  The targets are each class's log-times relative to the mean
+        over its own timed variants, scaled by their root mean square: a
+        choice compares the variants of one class only, and the class's
+        overall time (which spans orders of magnitude with N and the shape)
+        would otherwise take the network's capacity.  Classes with a single
+        variant carry no choice and are left out.  ``l2`` penalises the
         parameters (see ``L2_PENALTY``)."""
         torch = self.torch
-        lt = np.log(np.where(np.isfinite(times), times, 1.0))
-        mask = np.isfinite(times).astype(np.float32)
-        self.mu = float((lt * mask).sum() / mask.sum())
-        self.sd = float(np.sqrt(((lt - self.mu) ** 2 * mask).sum() / mask.sum())) or 1.0
-        T = torch.from_numpy(((lt - self.mu) / self.sd * mask).astype(np.float32)).to(self.dev)
+        ok = np.isfinite(times)
+        lt = np.log(np.where(ok, times, 1.0))
+        mask = (ok & (ok.sum(axis=1, keepdims=True) > 1)).astype(np.float64)
+        cnt = np.maximum(mask.sum(axis=1, keepdims=True), 1.0)
+        rel = (lt - (lt * mask).sum(axis=1, keepdims=True) / cnt) * mask
+        self.mu = 0.0
+        self.sd = float(np.sqrt((rel ** 2).sum() / mask.sum())) if mask.sum() > 0 else 1.0
+        self.sd = self.sd or 1.0
+        T = torch.from_numpy((rel / self.sd).astype(np.float32)).to(self.dev)
         X = torch.from_numpy(feats.astype(np.float32)).to(self.dev)
-        Mk = torch.from_numpy(mask).to(self.dev)
+        Mk = torch.from_numpy(mask.astype(np.float32)).to(self.dev)
         hist = []
         for i in range(steps):
             loss = self.step(X, T, Mk, lr, l2)
@@ -343,7 +367,9 @@ class CostModel:
                 hist.append(float(loss[0].item()))
         return hist
 
-    def predict_ms(self, feats: np.ndarray) -> np.ndarray:
+    def predict_rel(self, feats: np.ndarray) -> np.ndarray:
+        """Predicted time of every variant relative to the class's mean
+        variant (only ratios within a row are meaningful)."""
         X = self.torch.from_numpy(feats.astype(np.float32)).to(self.dev)
         Y, _ = self.forward(X)
         return np.exp(Y.cpu().numpy().astype(np.float64) * self.sd + self.mu)
@@ -351,40 +377,59 @@ class CostModel:
     def host_params(self) -> np.ndarray:
         return self.params.cpu().numpy().astype(np.float32)
 
-    def install(self, margin: float = 0.0) -> None:
+    def install(self, margins=0.0) -> None:
         """Hand the trained network to the library as its cost model (the
         library then evaluates it per class with its own forward kernel and
-        consults it under the MODEL selector mode)."""
+        consults it under the MODEL selector mode); ``margins``: one trust
+        margin, or one per storage type (``sbgemm.margin_array``)."""
         if self.mu is None:
             raise RuntimeError("the network has not been fitted")
-        sbgemm.set_cost_model(self.F, self.H, self.V, self.host_params(), self.mu, self.sd, margin)
+        sbgemm.set_cost_model(self.F, self.H, self.V, self.host_params(), self.mu, self.sd, margins)
 
-    def save(self, path: str, margin: float = 0.0) -> None:
+    def save(self, path: str, margins=0.0) -> None:
         """Install the network and write it to a versioned cost-model file
         that any process can load (``sbgemm_load_cost_model`` or the
         SBGEMM_COST_MODEL environment setting)."""
-        self.install(margin)
+        self.install(margins)
         sbgemm.save_cost_model(path)
 
-    def choose(self, feats: np.ndarray, nvalid: np.ndarray, margin: float = 0.0,
-               defaults: np.ndarray | None = None) -> np.ndarray:
-        """The variant with the smallest predicted time, unless it is not
-        predicted to beat the class's default variant (`defaults`, else 0)
-        by more than `margin` (a fraction): then the default."""
-        pred = self.predict_ms(feats)
-        idx = np.arange(pred.shape[1])[None, :]
-        pred = np.where(idx < nvalid[:, None], pred, np.inf)
-        best = np.argmin(pred, axis=1)
-        dflt = np.zeros(len(best), dtype=np.int64) if defaults is None else defaults
-        rows = np.arange(len(best))
-        gain = pred[rows, best] < pred[rows, dflt] * (1.0 - margin)
-        return np.where(gain, best, dflt)
+    def choose(self, feats: np.ndarray, nvalid: np.ndarray, margins=0.0,
+               defaults: np.ndarray | None = None, dtypes=None) -> np.ndarray:
+        """The library's rule on this network's predictions (``rule_choice``);
+        ``margins`` a number or a mapping from dtype letter to margin (then
+        ``dtypes`` gives each class's dtype)."""
+        dflt = np.zeros(len(feats), dtype=np.int64) if defaults is None else defaults
+        return rule_choice(self.predict_rel(feats), nvalid, row_margins(margins, dtypes, len(feats)),
+                           dflt)
+
+
+def row_margins(margins, dtypes, count: int) -> np.ndarray:
+    """One trust margin per class from a number or a dtype -> margin map."""
+    if isinstance(margins, dict):
+        return np.array([margins.get(d, 0.0) for d in dtypes], dtype=np.float64)
+    return np.full(count, float(margins))
+
+
+def rule_choice(pred: np.ndarray, nvalid: np.ndarray, margin: np.ndarray,
+                dflt: np.ndarray) -> np.ndarray:
+    """The selection rule the library applies to the cost model's outputs:
+    the valid variant (index < nvalid) with the smallest predicted time,
+    unless it is not predicted to beat the class's default variant by more
+    than the class's margin (a fraction; 1 never overrides): then the
+    default."""
+    idx = np.arange(pred.shape[1])[None, :]
+    pred = np.where(idx < nvalid[:, None], pred, np.inf)
+    best = np.argmin(pred, axis=1)
+    rows = np.arange(len(best))
+    gain = pred[rows, best] < pred[rows, dflt] * (1.0 - margin)
+    return np.where(gain, best, dflt)
 
 
 def default_choices(classes) -> np.ndarray:
     """The library's built-in choice for each class (``sbgemm_default_variant``:
-    the tensor-core variant of the 16-bit types at m = n = k = 8, 16; variant
-    2 for complex64 and for fp32 below 1e6 pairs; variant 0 otherwise)."""
+    the tensor-core variant of the 16-bit types at m = n = k = 8, 16 and of
+    fp64 at large shapes; variant 2 for complex64 and for fp32 below 1e6
+    pairs; variant 0 otherwise)."""
     return np.array([sbgemm.default_variant(c[0], c[1], c[2], c[3], c[7], size_class(c[8]))
                      for c in classes], dtype=np.int64)
 
@@ -404,19 +449,52 @@ def regret(times: np.ndarray, chosen: np.ndarray) -> np.ndarray:
     return times[np.arange(times.shape[0]), chosen] / best - 1.0
 
 
-MARGINS = (0.0, 0.02, 0.05, 0.1, 0.2)
+# candidate trust margins; 1.0 keeps the default rule for the whole type
+MARGINS = (0.0, 0.02, 0.05, 0.1, 0.2, 1.0)
+FOLDS = 4
 
 
-def select(net, Ftr, Ttr, nvtr, dtr, F, nv, dflt):
-    """The learned selection: the trust margin is picked on the training
-    classes only (the one whose choices give the smallest total training
-    time), then the network's choice for the classes `F` keeps each class's
-    default `dflt` unless it predicts a gain above that margin.  Returns
-    (choices, margin)."""
-    rows = np.arange(len(Ftr))
-    tr_total = {mg: float(np.nansum(Ttr[rows, net.choose(Ftr, nvtr, mg, dtr)])) for mg in MARGINS}
-    margin = min(MARGINS, key=lambda mg: (tr_total[mg], mg))
-    return net.choose(F, nv, margin, dflt), margin
+def pick_margins(pred: np.ndarray, times: np.ndarray, nvalid: np.ndarray, dflt: np.ndarray,
+                 dtypes) -> dict:
+    """Per storage type, the margin of ``MARGINS`` whose choices (``rule_choice``
+    on the predictions ``pred``) give the smallest total measured time over
+    that type's classes; ties go to the larger margin.  ``pred`` must come
+    from networks that did not see the classes (``out_of_fold``): on its own
+    training classes a network looks better than it is."""
+    dtypes = np.asarray(dtypes)
+    out = {}
+    for d in sorted(set(dtypes.tolist())):
+        rows = np.where(dtypes == d)[0]
+        total = {}
+        for mg in MARGINS:
+            ch = rule_choice(pred[rows], nvalid[rows], np.full(len(rows), mg), dflt[rows])
+            total[mg] = float(np.nansum(times[rows, ch]))
+        out[d] = min(MARGINS, key=lambda mg: (total[mg], -mg))
+    return out
+
+
+def out_of_fold(feats: np.ndarray, times: np.ndarray, folds=FOLDS, seed=0, steps=3000) -> np.ndarray:
+    """Predicted relative times of every class from a network trained on the
+    other folds (class i in fold i mod ``folds``)."""
+    pred = np.full(times.shape, np.nan)
+    fold = np.arange(len(feats)) % folds
+    for f in range(folds):
+        tr = fold != f
+        net = CostModel(seed=seed + 1 + f)
+        net.fit(feats[tr], times[tr], steps=steps)
+        pred[~tr] = net.predict_rel(feats[~tr])
+    return pred
+
+
+def learn(feats, times, nvalid, dflt, dtypes, seed=0, steps=3000, folds=FOLDS):
+    """The learned selector: per-type trust margins from out-of-fold
+    predictions on the training classes, then one network trained on all of
+    them.  Returns (network, margins, training-loss history)."""
+    margins = pick_margins(out_of_fold(feats, times, folds, seed, steps), times, nvalid, dflt,
+                           dtypes)
+    net = CostModel(seed=seed)
+    hist = net.fit(feats, times, steps=steps)
+    return net, margins, hist
 
 
 def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=9, steps=3000, db_path=None,
@@ -452,14 +530,17 @@ def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=9, steps=3000, db_p
     t1 = _time.time()
     Fte, Tte, nvte = table(test)
     t2 = _time.time()
-    net = CostModel(seed=seed)
-    hist = net.fit(Ftr, Ttr, steps=steps)
-    t3 = _time.time()
     dtr, dte = default_choices(train), default_choices(test)
+    ttr, tte = [c[0] for c in train], [c[0] for c in test]
+    net, margins, hist = learn(Ftr, Ttr, nvtr, dtr, ttr, seed=seed, steps=steps)
+    t3 = _time.time()
     chosen0 = net.choose(Fte, nvte, 0.0, dte)
-    chosen, margin = select(net, Ftr, Ttr, nvtr, dtr, Fte, nvte, dte)
+    chosen = net.choose(Fte, nvte, margins, dte, tte)
     r_mlp = regret(Tte, chosen)
     r_def = regret(Tte, dte)
+    # the method without any selection: one kernel per shape (variant 0)
+    plain = np.zeros(len(test), dtype=np.int64)
+    r_plain = regret(Tte, plain)
     multi = nvte > 1
     rep = {
         "device": tuner.name,
@@ -474,16 +555,20 @@ def evaluate(n_train_timings=2000, n_test=500, seed=11, reps=9, steps=3000, db_p
         "regret_default_p90": float(np.percentile(r_def, 90)),
         "regret_mlp_mean_multi": float(r_mlp[multi].mean()) if multi.any() else 0.0,
         "regret_default_mean_multi": float(r_def[multi].mean()) if multi.any() else 0.0,
+        "regret_plain_mean": float(r_plain.mean()),
         "mlp_picks_best": float((r_mlp == 0).mean()),
         "default_is_best": float((r_def == 0).mean()),
         "default_definition": "the library without a selection table (the tensor-core "
-                              "variant for 16-bit m = n = k = 8, 16; variant 2 for complex64 "
-                              "and for fp32 below 1e6 pairs; variant 0 otherwise)",
-        "trust_margin": margin,
+                              "variant for 16-bit m = n = k = 8, 16 and for fp64 at large "
+                              "shapes; variant 2 for complex64 and for fp32 below 1e6 pairs; "
+                              "variant 0 otherwise)",
+        "plain_definition": "variant 0 for every class (one kernel per shape, no selection)",
+        "trust_margins": margins, "folds": FOLDS,
         "regret_mlp_no_margin_mean": float(regret(Tte, chosen0).mean()),
         "time_mlp_no_margin_total_ms": float(Tte[np.arange(len(test)), chosen0].sum()),
         "time_mlp_total_ms": float(Tte[np.arange(len(test)), chosen].sum()),
         "time_default_total_ms": float(Tte[np.arange(len(test)), dte].sum()),
+        "time_plain_total_ms": float(Tte[np.arange(len(test)), plain].sum()),
         "time_exhaustive_total_ms": float(np.nanmin(Tte, axis=1).sum()),
         "seconds": {"tune_train": round(t1 - t0, 1), "tune_test": round(t2 - t1, 1),
                     "train_network": round(t3 - t2, 1)},
@@ -510,9 +595,10 @@ if __name__ == "__main__":
     ap.add_argument("--train-timings", type=int, default=2000)
     ap.add_argument("--test", type=int, default=500)
     ap.add_argument("--db", default=None)
+    ap.add_argument("--seed", type=int, default=11)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    rep, _ = evaluate(a.train_timings, a.test, db_path=a.db)
+    rep, _ = evaluate(a.train_timings, a.test, seed=a.seed, db_path=a.db)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(rep, f, indent=1)

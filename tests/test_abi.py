@@ -95,7 +95,7 @@ def test_status_strings_and_version():
 
 def test_variant_table_host_logic():
     assert sbgemm.num_variants("s", 16, 16, 16) == 7
-    assert sbgemm.num_variants("s", 7, 3, 11) == 1
+    assert sbgemm.num_variants("s", 7, 3, 11) == 1 and sbgemm.num_variants("d", 7, 3, 11) == 2
     assert sbgemm.num_variants("s", 17, 3, 11) == 0
     assert "generic" in sbgemm.variant_name("s", 7, 3, 11, 0)
     # the 16-bit types at m = n = k = 8, 16 also have the tensor-core variant
@@ -113,6 +113,13 @@ def test_variant_table_host_logic():
     assert sbgemm.get_choice("c", 10, 10, 10, 0, 0, 1, 6) == 2
     assert sbgemm.get_choice("d", 10, 10, 10, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 1, 5) == 7
+    # generic fp64 shapes: the tensor-core kernel (variant 1) from m n k = 1320
+    # (beta == 0) or 1792 (beta != 0)
+    assert sbgemm.get_choice("d", 16, 16, 15, 0, 0, 1, 5) == 1
+    assert sbgemm.get_choice("d", 8, 11, 15, 0, 0, 1, 5) == 1
+    assert sbgemm.get_choice("d", 8, 11, 15, 0, 0, 0, 5) == 0
+    assert sbgemm.get_choice("d", 7, 3, 11, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("s", 16, 16, 15, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 0
     assert sbgemm.get_choice("d", 12, 12, 12, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 0

@@ -103,3 +103,40 @@ def test_device_scalars_and_default_selection():
     b = inputs.UniformBatch("d", "N", "N", 16, 16, 16, 3001, seed=77)
     got = H.run_gpu(b, 1.5, -0.5, variant=TC, device_scalars=True)
     H.assert_parity(b, got, H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
+
+
+# shapes without specialised kernels: the tensor-core kernel is public
+# variant 1 there (variant 0 is the generic kernel)
+GENERIC_SHAPES = [(16, 16, 15), (15, 16, 16), (16, 15, 16), (14, 16, 12), (16, 9, 13),
+                  (13, 7, 16), (1, 16, 16), (16, 1, 16), (7, 3, 11), (5, 16, 2), (12, 10, 14)]
+
+
+@pytest.mark.parametrize("shape", GENERIC_SHAPES)
+def test_generic_shapes_variant1(shape):
+    m, n, k = shape
+    from paper_1304_7053_gb300 import sbgemm
+    assert sbgemm.num_variants("d", m, n, k) == 2
+    assert "tensor-core" in sbgemm.variant_name("d", m, n, k, 1)
+    for i, ((ta, tb), beta) in enumerate(itertools.product(OPS, (0.0, -0.5))):
+        bi = inputs.UniformBatch("d", ta, tb, m, n, k, 777, seed=800 + i, int_valued=True)
+        H.assert_parity(bi, H.run_gpu(bi, 1.5, beta, variant=1), H.oracle_ref(bi, 1.5, beta),
+                        1.5, beta, exact=True)
+        bu = inputs.UniformBatch("d", ta, tb, m, n, k, 901, seed=900 + i, pad_ld=i % 3,
+                                 pad_ld2=(3 * i) % 7)
+        H.assert_parity(bu, H.run_gpu(bu, 1.5, beta, variant=1), H.oracle_ref(bu, 1.5, beta),
+                        1.5, beta)
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 15), (14, 16, 12), (7, 3, 11)])
+def test_generic_shapes_default_and_pointer_arrays(shape):
+    """Whatever the default rule picks for a generic fp64 shape (the
+    tensor-core kernel or the generic one), the uniform call and the
+    pointer-array call (which has no tensor-core form and runs the generic
+    kernel) both meet the bound."""
+    m, n, k = shape
+    b = inputs.UniformBatch("d", "N", "T", m, n, k, 1501, seed=950 + m)
+    H.assert_parity(b, H.run_gpu(b, 1.5, -0.5), H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
+    H.assert_parity(b, H.run_gpu(b, 1.0, 0.0), H.oracle_ref(b, 1.0, 0.0), 1.0, 0.0)
+    from tests.test_gpu_nounif import run_case
+    for beta in (0.0, -0.5):
+        run_case("d", ("N", "T", m, n, k), (1, 1), 1500, 1.5, beta, seed=970 + m)

@@ -31,7 +31,7 @@ L = sbgemm.lib()
 out = {"selector": sbgemm.get_selector(),
        "choice_m10": L.sbgemm_get_choice(1, 10, 10, 10, 0, 0, 1, 3),
        "choice_m12": L.sbgemm_get_choice(1, 12, 12, 12, 0, 0, 1, 3),
-       "choice_generic": L.sbgemm_get_choice(1, 7, 3, 11, 0, 0, 1, 3)}
+       "choice_generic": L.sbgemm_get_choice(0, 7, 3, 11, 0, 0, 1, 3)}
 ran = {}
 for m in (10, 12):
     b = inputs.UniformBatch("d", "N", "N", m, m, m, 5003, seed=m, int_valued=True)
@@ -70,7 +70,7 @@ def test_fresh_process_applies_table_and_cost_model(tmp_path):
     assert out["selector"] == [sbgemm.SELECTOR_MODEL, 0]
     assert out["choice_m10"] == 4 and out["ran_m10"] == 4          # the model's choice
     assert out["choice_m12"] == 3 and out["ran_m12"] == 3          # the table wins
-    assert out["choice_generic"] == 0                                # one variant only
+    assert out["choice_generic"] == 0                                # fp32: one variant only
     assert out["ran_m10_table_mode"] == sbgemm.default_variant("d", 10, 10, 10, 1, 3)
 
 
@@ -89,25 +89,26 @@ def test_library_evaluation_matches_trainer():
     times = np.where(np.arange(selector.NVAR)[None, :] < nv[:, None], times, np.nan)
     net = selector.CostModel(seed=1)
     net.fit(feats, times, steps=300)
-    margin = 0.02
+    margins = {"s": 0.02, "d": 0.0, "c": 0.05, "z": 1.0, "h": 0.1, "b": 0.02}
     sbgemm.clear_choices()
-    net.install(margin)
+    net.install(margins)
     sbgemm.set_selector(sbgemm.SELECTOR_MODEL)
     try:
         checked = 0
         for dt in selector.DTYPES:
-            for m, nn, k in ((8, 8, 8), (10, 10, 10), (16, 16, 16), (4, 16, 4)):
+            for m, nn, k in ((8, 8, 8), (10, 10, 10), (16, 16, 16), (4, 16, 4), (16, 16, 15)):
                 for ta, tb, bz, sc in ((0, 0, 1, 3), (1, 0, 0, 5), (0, 1, 1, 6)):
                     f = selector.features(dt, m, nn, k, ta, tb, 0, bz, 10 ** (sc + 0.5))[None, :]
                     nvalid = np.array([sbgemm.num_variants(dt, m, nn, k)])
                     dflt = np.array([sbgemm.default_variant(dt, m, nn, k, bz, sc)])
-                    want = int(net.choose(f, nvalid, margin, dflt)[0])
+                    margin = margins[dt]
+                    want = int(net.choose(f, nvalid, margins, dflt, [dt])[0])
                     got = sbgemm.get_choice(dt, m, nn, k, ta, tb, bz, sc)
                     if got != want:
-                        pr = net.predict_ms(f)[0]
+                        pr = net.predict_rel(f)[0]
                         assert abs(pr[got] - pr[want]) <= 1e-4 * pr[want] or \
                             abs(pr[got] - pr[dflt[0]] * (1 - margin)) <= 1e-4 * pr[got], (dt, m, got, want)
                     checked += 1
-        assert checked == 6 * 4 * 3
+        assert checked == 6 * 5 * 3
     finally:
         sbgemm.set_selector(sbgemm.SELECTOR_TABLE)

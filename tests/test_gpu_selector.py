@@ -88,38 +88,23 @@ def test_adam_matches_reference():
         assert np.abs(g[name] - pr[name]).max() < 1e-3, name
 
 
-def test_learned_selector_regret():
-    """Train on autotuner timings of random problem classes, evaluate on
-    held-out classes with the library's selection rule (trust margin picked
-    on the training classes): the network's mean regret (vs the exhaustive
-    best) must not exceed that of the library's default choice (no selection
-    table) by more than 2 points, nor the total time of its choices the
-    default's by more than 2%."""
-    db = selector.TimingDB(None)
-    tuner = selector.Tuner(db, reps=5, flush_bytes=192 << 20)
-    train = selector.random_classes(160, seed=11)
-    test = selector.random_classes(60, seed=12)
-
-    def table(classes):
-        F = np.stack([selector.features(*c) for c in classes])
-        Tm = np.full((len(classes), selector.NVAR), np.nan)
-        nv = np.zeros(len(classes), dtype=np.int64)
-        for i, c in enumerate(classes):
-            t = tuner.time_class(*c)
-            Tm[i, :len(t)] = t
-            nv[i] = len(t)
-        return F, Tm, nv
-
-    Ftr, Ttr, nvtr = table(train)
-    Fte, Tte, nvte = table(test)
-    net = selector.CostModel(seed=1)
-    hist = net.fit(Ftr, Ttr, steps=1500)
-    assert hist[-1] < hist[0]
-    dtr, dte = selector.default_choices(train), selector.default_choices(test)
-    chosen, _ = selector.select(net, Ftr, Ttr, nvtr, dtr, Fte, nvte, dte)
-    r_mlp = selector.regret(Tte, chosen)
-    r_def = selector.regret(Tte, dte)
-    assert np.all(np.isfinite(r_mlp))
-    assert r_mlp.mean() <= r_def.mean() + 0.02, (r_mlp.mean(), r_def.mean())
-    rows = np.arange(len(test))
-    assert Tte[rows, chosen].sum() <= 1.02 * Tte[rows, dte].sum()
+def test_learned_selector_gain():
+    """What the trained network gains, on 500 held-out problem classes timed
+    by the exhaustive autotuner (the judge of regret = t(chosen) / t(best)
+    - 1), after training on about 2000 autotuner timings of other random
+    classes, with per-type trust margins picked on out-of-fold predictions:
+    - against the method without it (one kernel per shape, variant 0 for
+      every class): a lower total time and a lower mean regret;
+    - against the library's hand-written rule (measured on this GPU, which
+      the network is not told): a lower mean regret, and a total time no
+      higher than the rule's plus 0.1% (the total is dominated by the
+      largest classes, where both mostly pick the same variant; over four
+      seeds the network's total was 0.01-0.47 ms below the rule's out of
+      90-180 ms)."""
+    rep, _ = selector.evaluate(n_train_timings=2000, n_test=500, seed=11, log=lambda s: None)
+    assert rep["loss_last"] < rep["loss_first"]
+    assert rep["time_mlp_total_ms"] < rep["time_plain_total_ms"], rep
+    assert rep["regret_mlp_mean"] < rep["regret_plain_mean"], rep
+    assert rep["regret_mlp_mean"] < rep["regret_default_mean"], rep
+    assert rep["time_mlp_total_ms"] <= 1.001 * rep["time_default_total_ms"], rep
+    assert rep["time_exhaustive_total_ms"] <= rep["time_mlp_total_ms"]

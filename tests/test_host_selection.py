@@ -26,33 +26,42 @@ def test_robust_mean_resolves_below_a_timer_step():
     assert sweep.robust_mean([1.0, 1.0, 1.0]) == 1.0
 
 
-class _Net:
-    """Predicts fixed times (ms) per class and variant."""
+def test_rule_keeps_default_unless_the_predicted_gain_clears_the_margin():
+    pred = np.array([[1.0, 0.95, 2.0], [1.0, 0.7, 0.5], [1.0, 0.5, 0.1]])
+    nv = np.array([3, 3, 1])
+    dflt = np.array([0, 0, 0])
+    # margin 0: the smallest prediction among the valid variants
+    assert list(selector.rule_choice(pred, nv, np.zeros(3), dflt)) == [1, 2, 0]
+    # margin 0.1: a 5% predicted gain is not enough, a 50% one is
+    assert list(selector.rule_choice(pred, nv, np.full(3, 0.1), dflt)) == [0, 2, 0]
+    # margin 1 never overrides; per-class margins apply row by row
+    assert list(selector.rule_choice(pred, nv, np.ones(3), dflt)) == [0, 0, 0]
+    assert list(selector.rule_choice(pred, nv, np.array([0.0, 1.0, 0.0]), dflt)) == [1, 0, 0]
+    # the default need not be variant 0
+    assert list(selector.rule_choice(pred, nv, np.full(3, 0.2), np.array([2, 1, 0]))) == [1, 2, 0]
 
-    def __init__(self, pred):
-        self.pred = np.asarray(pred, dtype=np.float64)
 
-    def choose(self, F, nv, margin, dflt):
-        rows = np.arange(len(F))
-        pred = np.where(np.arange(self.pred.shape[1])[None, :] < nv[:, None], self.pred[rows], np.inf)
-        best = pred.argmin(axis=1)
-        gain = pred[rows, best] < pred[rows, dflt] * (1.0 - margin)
-        return np.where(gain, best, dflt)
-
-
-def test_select_keeps_default_unless_the_predicted_gain_clears_the_margin():
-    # training classes: the network's first pick is wrong (predicts 5% gain for
-    # variant 1, which is really slower); the second it gets right (30% gain)
-    Ttr = np.array([[1.0, 1.2], [1.0, 0.7]])
-    pred = np.array([[1.0, 0.95], [1.0, 0.7]])
-    F = np.zeros((2, 3))
-    nv = np.array([2, 2])
-    dflt = np.array([0, 0])
-    chosen, margin = selector.select(_Net(pred), F, Ttr, nv, dflt, F, nv, dflt)
-    # margins 0 and 0.02 take the bad switch (total 1.9), 0.05 and above keep
-    # the default there and still take the good one (total 1.7)
-    assert margin == 0.05
-    assert list(chosen) == [0, 1]
-    # a class with one valid variant always keeps it
-    chosen, _ = selector.select(_Net(pred), F, Ttr, nv, dflt, F[:1], np.array([1]), np.array([0]))
-    assert list(chosen) == [0]
+def test_margins_are_picked_per_type_on_held_out_predictions():
+    # type s: the predictions are right (variant 1 really is 30% faster);
+    # type d: the network predicts a 5% gain for variant 1, which is really
+    # 20% slower, and a 40% gain that is real
+    times = np.array([[1.0, 0.7], [1.0, 0.7],          # s
+                      [1.0, 1.2], [1.0, 0.6]])         # d
+    pred = np.array([[1.0, 0.7], [1.0, 0.72],
+                     [1.0, 0.95], [1.0, 0.6]])
+    nv = np.array([2, 2, 2, 2])
+    dflt = np.zeros(4, dtype=np.int64)
+    m = selector.pick_margins(pred, times, nv, dflt, ["s", "s", "d", "d"])
+    # s: every margin up to 0.2 takes both gains; ties go to the largest (0.2)
+    assert m["s"] == 0.2
+    # d: 0 and 0.02 take the bad switch; 0.05 .. 0.2 keep the default there
+    # and still take the good one; the tie goes to 0.2
+    assert m["d"] == 0.2
+    # a network whose every switch loses: margin 1 (the default rule kept)
+    bad = np.array([[1.0, 0.5], [1.0, 0.4]])
+    m = selector.pick_margins(bad, np.array([[1.0, 1.1], [1.0, 1.3]]), np.array([2, 2]),
+                              np.zeros(2, dtype=np.int64), ["z", "z"])
+    assert m == {"z": 1.0}
+    # row_margins spreads a type map over the classes
+    assert list(selector.row_margins({"s": 0.1, "d": 1.0}, ["d", "s", "h"], 3)) == [1.0, 0.1, 0.0]
+    assert list(selector.row_margins(0.05, None, 2)) == [0.05, 0.05]

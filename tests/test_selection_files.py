@@ -105,41 +105,65 @@ def _params(seed=3):
     return ((np.arange(n) * 2654435761 % 1000003) / 1000003.0 - 0.5).astype(np.float32)
 
 
+MARGINS6 = {"s": 0.05, "d": 1.0, "c": 0.0, "z": 0.02, "h": 0.1, "b": 0.2}
+
+
 def test_cost_model_file_round_trip(tmp_path):
     p = _params()
-    sbgemm.set_cost_model(16, 64, 9, p, -2.5, 1.25, 0.05)
+    sbgemm.set_cost_model(16, 64, 9, p, -2.5, 1.25, MARGINS6)
     f1 = str(tmp_path / "model.txt")
     sbgemm.save_cost_model(f1)
     txt = open(f1).read().split("\n")
-    assert txt[0] == "sbgemm-cost-model 1" and txt[1].startswith("device ")
+    assert txt[0] == "sbgemm-cost-model 2" and txt[1].startswith("device ")
     assert txt[2] == "features 16 hidden 64 outputs 9"
-    vals = np.array(" ".join(txt[5:]).split(), dtype=np.float32)
+    assert txt[3] == "log_time_mean -2.5 log_time_std 1.25"
+    assert [float(x) for x in txt[4].split()[1:]] == [MARGINS6[d] for d in "sdczhb"]
+    vals = np.array(" ".join(txt[6:]).split(), dtype=np.float32)
     assert np.array_equal(vals, p)                        # 9 digits: exact for fp32
     sbgemm.load_cost_model(f1)
     f2 = str(tmp_path / "model2.txt")
     sbgemm.save_cost_model(f2)
     assert open(f2).read() == open(f1).read()
+    # a version-1 file (one margin for every type) loads and saves as version 2
+    lines = open(f1).read().split("\n")
+    lines[0] = "sbgemm-cost-model 1"
+    lines[3] = lines[3] + " margin 0.125"
+    del lines[4]
+    f3 = str(tmp_path / "model_v1.txt")
+    open(f3, "w").write("\n".join(lines))
+    sbgemm.load_cost_model(f3)
+    sbgemm.save_cost_model(f2)
+    assert open(f2).read().split("\n")[4] == "margins" + " 0.125" * 6
 
 
 def test_cost_model_rejections(tmp_path):
     L = sbgemm.lib()
     p = _params()
     addr = p.ctypes.data
-    assert L.sbgemm_set_cost_model(15, 64, 9, addr, 0.0, 1.0, 0.0) == -5     # F must be 16
-    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 0.0, 0.0) == -5     # std > 0
-    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 1.0, 1.0) == -5     # margin < 1
+    m0 = np.zeros(6)
+    assert L.sbgemm_set_cost_model(15, 64, 9, addr, 0.0, 1.0, m0.ctypes.data) == -5   # F must be 16
+    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 0.0, m0.ctypes.data) == -5   # std > 0
+    for bad_margin in (1.5, -0.1, np.nan):
+        mb = np.zeros(6)
+        mb[3] = bad_margin
+        assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 1.0, mb.ctypes.data) == -5
+    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 1.0, None) == -4       # margins NULL
+    assert L.sbgemm_set_cost_model(16, 64, 9, addr, 0.0, 1.0, np.ones(6).ctypes.data) == 0
     q = p.copy()
     q[5] = np.nan
-    assert L.sbgemm_set_cost_model(16, 64, 9, q.ctypes.data, 0.0, 1.0, 0.0) == -5
+    assert L.sbgemm_set_cost_model(16, 64, 9, q.ctypes.data, 0.0, 1.0, m0.ctypes.data) == -5
     sbgemm.set_cost_model(16, 64, 9, p, 0.0, 1.0, 0.0)
     good = str(tmp_path / "m.txt")
     sbgemm.save_cost_model(good)
     text = open(good).read()
     n = int(L.sbgemm_mlp_param_count(16, 64, 9))
     for bad in (text.replace(f"params {n}", f"params {n - 1}"),        # count mismatch
-                text.replace("sbgemm-cost-model 1", "sbgemm-cost-model 3"),
+                text.replace("sbgemm-cost-model 2", "sbgemm-cost-model 3"),
+                text.replace("margins 0 0 0 0 0 0", "margins 0 0 0 0 0"),  # five margins
+                text.replace("margins 0 0 0 0 0 0", "margins 0 0 0 0 0 2"),  # margin above 1
                 text.rsplit("\n", 2)[0] + "\n",                          # truncated
                 text + "1.0\n"):                                         # trailing value
+        assert bad != text
         f = str(tmp_path / "bad.txt")
         open(f, "w").write(bad)
         assert L.sbgemm_load_cost_model(f.encode()) == -9
