@@ -271,12 +271,13 @@ sbgemm_status sbgemm_gemm_multi_nounif(int type, char transa, char transb, int m
 /* Number of kernel variants a (type, m, n, k) problem can run with (0 for
  * an invalid request).  Shapes with specialised kernels have six settings of
  * the pipelined kernel (0..5) and the generic kernel (6); the 16-bit types at
- * m = n = k = 8, 12, 16 and real fp64 add variant 7, the tensor-core kernel
- * (for fp64: operands split into exact 8-bit digits whose products run on
- * the binary16 MMA path, recombined exactly; entries whose accuracy the
- * split cannot guarantee are recomputed with fp64 FMAs).  Other shapes have
- * the generic kernel as variant 0 and, for real fp64 only, the same
- * tensor-core kernel as variant 1. */
+ * m = n = k = 8, 12, 16 and real and complex fp64 add variant 7, the
+ * tensor-core kernel (for fp64 and complex128: operands split into exact
+ * 8-bit digits whose products run on the binary16 MMA path, recombined
+ * exactly; entries whose accuracy the split cannot guarantee are recomputed
+ * with fp64 FMAs).  Other shapes have the generic kernel as variant 0 and,
+ * for real and complex fp64 only, the same tensor-core kernel as
+ * variant 1. */
 int sbgemm_num_variants(int type, int m, int n, int k);
 
 /* Human-readable description of a variant (static storage, never NULL). */

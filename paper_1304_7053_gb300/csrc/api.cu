@@ -87,11 +87,12 @@ bool host_scalar_zero(int type, const void* p) {
 
 // Map a public variant index to the internal one.  Shapes with specialised
 // kernels use the internal index as is; the other shapes have the generic
-// kernel (internal kNumPipeVariants) as variant 0 and, for real fp64, the
-// tensor-core kernel (internal kMmaVariant) as variant 1.
+// kernel (internal kNumPipeVariants) as variant 0 and, for real and complex
+// fp64, the tensor-core kernel (internal kMmaVariant) as variant 1.
 int internal_variant(int type, int m, int n, int k, int v) {
     if (has_specialized(0, m, n, k)) return v;
-    return type == SBGEMM_TYPE_D && v == 1 ? kMmaVariant : kNumPipeVariants;
+    return (type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z) && v == 1 ? kMmaVariant
+                                                                       : kNumPipeVariants;
 }
 
 sbgemm_status run_typed(const Req& r) {
@@ -310,7 +311,7 @@ const char* sbgemm_variant_name(int type, int m, int n, int k, int variant) {
         "pipe tile32K st2 occ-max", "pipe tile16K st3 1cta/sm (st2 for fp64)",
         "pipe tile4K st4 occ-max", "pipe tile24K st3 2cta/sm",
         "generic thread-per-entry",
-        "tensor-core: mma.sync for 16-bit N/N flat; 8-bit digit products for fp64; else variant 0"};
+        "tensor-core: mma.sync for 16-bit N/N flat; 8-bit digit products for fp64 and complex128; else variant 0"};
     const int nv = sbgemm_num_variants(type, m, n, k);
     if (variant < 0 || variant >= nv) return "invalid";
     return names[sbg::internal_variant(type, m, n, k, variant)];

@@ -43,13 +43,14 @@ struct LaunchOpts {
 constexpr int kNumPipeVariants = 6;
 // Variant after the generic kernel: the tensor-core kernel of the 16-bit
 // types (csrc/mma16.cuh), for m = n = k = 8, 12 or 16, op N/N, flat layouts,
-// and of real fp64 (csrc/ozaki.cuh, any op and layout of the uniform form);
-// any other request given this variant runs variant 0.
+// and of real and complex fp64 (csrc/ozaki.cuh, csrc/ozaki_z.cuh, any op
+// and layout of the uniform form); any other request given this variant
+// runs variant 0.
 constexpr int kMmaVariant = kNumPipeVariants + 1;
 sbgemm_status run_mma16(const Req& r);   // mma16.cu
 bool mma16_ok(const Req& r);
-// The same variant index for real fp64 runs the tensor-core kernel that
-// splits fp64 operands into exact 8-bit digits (csrc/ozaki.cuh).
+// The same variant index for real and complex fp64 runs the tensor-core
+// kernels that split fp64 operands into exact 8-bit digits.
 sbgemm_status run_ozaki(const Req& r);   // ozaki.cu
 bool ozaki_ok(const Req& r);
 inline LaunchOpts pipe_variant(int v, int type_code = 0) {

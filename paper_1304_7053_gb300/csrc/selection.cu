@@ -55,9 +55,10 @@ std::once_flag g_env_once;
 std::atomic<int> g_env_status{0};
 
 // the tensor-core variant: 16-bit storage at m = n = k = 8, 12, 16, and real
-// fp64 (digit-split products) on every shape with specialised kernels
+// and complex fp64 (digit-split products) on every shape with specialised
+// kernels
 bool has_mma_variant(int type, int m, int n, int k) {
-    if (type == SBGEMM_TYPE_D) return has_specialized(0, m, n, k);
+    if (type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z) return has_specialized(0, m, n, k);
     return (type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && m == n && n == k &&
            (m == 8 || m == 12 || m == 16);
 }
@@ -346,8 +347,9 @@ int size_class(int batch) {
 int variants_for(int type, int m, int n, int k) {
     if (m < 1 || n < 1 || k < 1 || m > 16 || n > 16 || k > 16) return 0;
     // shapes without specialised kernels: the generic kernel, and for real
-    // fp64 also the tensor-core kernel (public variant 1)
-    if (!has_specialized(0, m, n, k)) return type == SBGEMM_TYPE_D ? 2 : 1;
+    // and complex fp64 also the tensor-core kernel (public variant 1)
+    if (!has_specialized(0, m, n, k))
+        return type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z ? 2 : 1;
     return has_mma_variant(type, m, n, k) ? kMmaVariant + 1 : kNumPipeVariants + 1;
 }
 
@@ -376,15 +378,33 @@ int variants_for(int type, int m, int n, int k) {
 //   15, 16}, op N/N, N = 1e5, this rule took 101.4 / 123.7 ms in total
 //   (beta == 0 / beta = -0.5) against 100.6 / 121.0 ms for the best
 //   variant of each shape and 129.5 / 135.3 ms for the generic kernel alone;
+// - the tensor-core kernel for complex128 at m = n = k = 13..16, at 12 with
+//   beta == 0, and at 16 x 8 x 16: with alpha = 1.5 at N = 1e5 it took
+//   1.21 / 1.22 / 1.23 / 1.20 ms for m = 13 / 14 / 15 / 16 against 1.95 /
+//   2.25 / 2.49 / 2.87 ms on the fp64 FMA pipe with beta = 0 (1.6-2.4x;
+//   1.35-2.2x with beta = -0.5), 1.20 against 1.28 ms at m = 12 (even with
+//   beta != 0), and 0.80 against 1.88 ms for 16 x 8 x 16 (op(A) = T,
+//   beta = 1); on the complex128 shapes without specialised kernels, the
+//   tensor-core kernel (public variant 1) when m n k >= 1144 (beta == 0) or
+//   1232: over the 334 such shapes of the fp64 rule's grid, op N/N, N = 1e5,
+//   289.8 / 336.9 ms in total against 288.4 / 334.6 ms for the best variant
+//   of each and 412.2 / 452.9 ms for the generic kernel alone;
 // - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
 //   no difference; the 16-bit CUDA-core kernels were mixed).
 int default_variant(int type, int m, int n, int k, int bz, int sc) {
+    if (type == SBGEMM_TYPE_Z) {
+        if (!has_specialized(0, m, n, k)) return m * n * k >= (bz ? 1144 : 1232) ? 1 : 0;
+        if (m == n && n == k && (m >= 13 || (m == 12 && bz))) return kMmaVariant;
+        if (m == 16 && n == 8 && k == 16) return kMmaVariant;
+    }
     if (type == SBGEMM_TYPE_D) {
         if (!has_specialized(0, m, n, k)) return m * n * k >= (bz ? 1320 : 1792) ? 1 : 0;
         if (m == n && n == k && (m >= 15 || (m >= 13 && bz))) return kMmaVariant;
         if (m == 16 && n == 8 && k == 16) return kMmaVariant;
     }
-    if (has_mma_variant(type, m, n, k) && type != SBGEMM_TYPE_D && m != 12) return kMmaVariant;
+    if ((type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && has_mma_variant(type, m, n, k) &&
+        m != 12)
+        return kMmaVariant;
     if (!has_specialized(0, m, n, k)) return 0;
     if (type == SBGEMM_TYPE_C || (type == SBGEMM_TYPE_S && sc <= 5)) return 2;
     return 0;

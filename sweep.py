@@ -28,8 +28,8 @@ cublasSgemmGroupedBatched on the fp32 mixed-size batch; ``once`` (only when
 named) makes one untimed call per type and
 size (fp32 and fp64, m = 8..16, N = 1e5, op N/N, alpha = 1, beta = 0, L2
 evicted before each): the launches a kernel-level profile reads.  ``fp64tc``
-(only when named) times real fp64 on the fp64 FMA kernel (variant 0) and on
-the tensor-core kernel (variant 7).
+(only when named) times real and complex fp64 (``--fp64tc-types``) on the
+fp64 FMA kernel (variant 0) and on the tensor-core kernel (variant 7).
 """
 from __future__ import annotations
 
@@ -443,6 +443,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default="sweep.json")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--fp64tc-types", default="d,z", type=lambda v: v.split(","),
+                    help="types of the fp64tc section (d, z)")
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
     ap.add_argument("--sections", default="small,fixed,ops,fem,interface,shared_a,16bit",
                     help="comma-separated subset of the sections to run "
@@ -554,18 +556,19 @@ def main(argv=None):
     # real fp64: the fp64 FMA kernel (variant 0) against the tensor-core
     # kernel (variant 7), square N/N and the FEM shapes, alpha = 1.5
     if "fp64tc" in want:
-        for N in (100_000, 1_000_000):
-            for (m, n, k, ta, beta) in [(s_, s_, s_, "N", b_) for s_ in sizes for b_ in (0.0, -0.5)] + \
-                    [(4, 16, 4, "T", 1.0), (9, 16, 9, "T", 1.0), (16, 8, 16, "T", 1.0),
-                     (3, 9, 3, "T", 1.0), (16, 16, 1, "T", 1.0)]:
-                if N == 1_000_000 and (m != n or m not in (8, 12, 13, 14, 15, 16)):
-                    continue
-                ms0 = time_ours(pools, "d", ta, "N", m, n, k, N, 1.5, beta, args.reps, variant=0)
-                ms7 = time_ours(pools, "d", ta, "N", m, n, k, N, 1.5, beta, args.reps, variant=7)
-                r = row("d", ta, "N", m, n, k, N, beta, ms7)
-                r["fma_ms"] = round(ms0, 5)
-                r["tensor_over_fma_speedup"] = round(ms0 / ms7, 2)
-                emit(r, "fp64tc")
+        for dt in args.fp64tc_types:
+            for N in (100_000, 1_000_000):
+                for (m, n, k, ta, beta) in [(s_, s_, s_, "N", b_) for s_ in sizes for b_ in (0.0, -0.5)] + \
+                        [(4, 16, 4, "T", 1.0), (9, 16, 9, "T", 1.0), (16, 8, 16, "T", 1.0),
+                         (3, 9, 3, "T", 1.0), (16, 16, 1, "T", 1.0)]:
+                    if N == 1_000_000 and (m != n or m not in (8, 12, 13, 14, 15, 16)):
+                        continue
+                    ms0 = time_ours(pools, dt, ta, "N", m, n, k, N, 1.5, beta, args.reps, variant=0)
+                    ms7 = time_ours(pools, dt, ta, "N", m, n, k, N, 1.5, beta, args.reps, variant=7)
+                    r = row(dt, ta, "N", m, n, k, N, beta, ms7)
+                    r["fma_ms"] = round(ms0, 5)
+                    r["tensor_over_fma_speedup"] = round(ms0 / ms7, 2)
+                    emit(r, "fp64tc")
     # 16-bit storage
     if "16bit" in want:
         for dtype in ("h", "b"):

@@ -101,7 +101,8 @@ def test_variant_table_host_logic():
     # the 16-bit types at m = n = k = 8, 16 also have the tensor-core variant
     assert sbgemm.num_variants("b", 16, 16, 16) == 8 and sbgemm.num_variants("h", 8, 8, 8) == 8
     assert sbgemm.num_variants("b", 12, 12, 12) == 8 and sbgemm.num_variants("d", 16, 16, 16) == 8
-    assert sbgemm.num_variants("z", 16, 16, 16) == 7 and sbgemm.num_variants("d", 9, 16, 9) == 8
+    assert sbgemm.num_variants("z", 16, 16, 16) == 8 and sbgemm.num_variants("d", 9, 16, 9) == 8
+    assert sbgemm.num_variants("z", 7, 3, 11) == 2 and sbgemm.num_variants("c", 7, 3, 11) == 1
     assert sbgemm.num_variants("h", 10, 10, 10) == 7
     assert "tensor-core" in sbgemm.variant_name("h", 16, 16, 16, 7)
     sbgemm.clear_choices()
@@ -120,9 +121,19 @@ def test_variant_table_host_logic():
     assert sbgemm.get_choice("d", 8, 11, 15, 0, 0, 0, 5) == 0
     assert sbgemm.get_choice("d", 7, 3, 11, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("s", 16, 16, 15, 0, 0, 1, 5) == 0
+    # complex128: the tensor cores at m = n = k >= 13, 12 with beta == 0, and
+    # 16 x 8 x 16
+    assert sbgemm.get_choice("z", 13, 13, 13, 0, 0, 0, 5) == 7
+    assert sbgemm.get_choice("z", 12, 12, 12, 0, 0, 1, 5) == 7
+    assert sbgemm.get_choice("z", 12, 12, 12, 0, 0, 0, 5) == 0
+    assert sbgemm.get_choice("z", 16, 8, 16, 1, 0, 0, 5) == 7
+    assert sbgemm.get_choice("z", 11, 11, 11, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("z", 16, 16, 15, 0, 0, 1, 5) == 1
+    assert sbgemm.get_choice("z", 8, 11, 13, 0, 0, 1, 5) == 1
+    assert sbgemm.get_choice("z", 8, 11, 13, 0, 0, 0, 5) == 0
     assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 0
     assert sbgemm.get_choice("d", 12, 12, 12, 0, 0, 1, 5) == 0
-    assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 7
     assert sbgemm.get_choice("h", 16, 16, 16, 0, 0, 1, 6) == 7
     assert sbgemm.get_choice("h", 12, 12, 12, 0, 0, 1, 6) == 0
     assert sbgemm.get_choice("s", 7, 3, 11, 0, 0, 1, 5) == 0
