@@ -26,7 +26,7 @@ launch configuration of the grouped call on the fp32 and fp64 sizes 1..16
 workload; ``vbatch`` (only when named) compares the variable-size plan with
 cublasSgemmGroupedBatched on the fp32 mixed-size batch; ``once`` (only when
 named) makes one untimed call per type and
-size (fp32 and fp64, m = 8..16, N = 1e5, op N/N, alpha = 1, beta = 0, L2
+size (fp32, fp64 and complex128, m = 8..16, N = 1e5, op N/N, alpha = 1, beta = 0, L2
 evicted before each): the launches a kernel-level profile reads.  ``fp64tc``
 (only when named) times real and complex fp64 (``--fp64tc-types``) on the
 fp64 FMA kernel (variant 0) and on the tensor-core kernel (variant 7).
@@ -469,8 +469,8 @@ def main(argv=None):
                 json.dump(rows, f)
             return rows
     if "once" in want:
-        pools = Pools(8 * 256 * 100_000 + 4096, dev)
-        for dtype in ("s", "d"):
+        pools = Pools(16 * 256 * 100_000 + 4096, dev)
+        for dtype in ("s", "d", "z"):
             for m in range(8, 17):
                 S = m * m
                 pools.evict()
