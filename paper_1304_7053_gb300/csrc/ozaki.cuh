@@ -114,6 +114,15 @@ __device__ __forceinline__ int oz_int(float f) {
     return __float_as_int(f + 12582912.0f) - 0x4B400000;
 }
 
+// An accumulator that starts at kOzBias = 1.5 * 2^23 holds bias + v for the
+// integer v it has summed (|v| < 2^22): every value lies in [2^23, 2^24),
+// where fp32 represents each integer exactly, so the MMAs stay exact and v
+// is the bit pattern minus that of the bias (no add needed to read it back).
+constexpr float kOzBias = 12582912.0f;
+__device__ __forceinline__ int oz_unbias(float f) {
+    return __float_as_int(f) - 0x4B400000;
+}
+
 // The double nearest to (S_hi 2^32 + S_lo) 2^(sc - 32) (|S_hi|, |S_lo| <
 // 2^48), assembled with integer operations (round to nearest even); results
 // outside the normal range go through ldexp.
@@ -267,6 +276,18 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
             if (8 * h >= n) break;
             long long shi[4], slo[4];
             unsigned use = 0;
+            // the old C of this half's outputs, loaded before the products so
+            // the load latency is hidden behind them (general epilogue only)
+            double cold[4] = {0.0, 0.0, 0.0, 0.0};
+            if constexpr (EM == 2) {
+                if (!beta_zero) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int i = gq + 8 * (r >> 1), j = 2 * tq + (r & 1) + 8 * h;
+                        if (i < m && j < n) cold[r] = Cp[i + (long long)g.ldc * j];
+                    }
+                }
+            }
             if (!nonfinite) {
                 const int eb = h ? eb1 : eb0;
                 unsigned long long xb[4];
@@ -304,7 +325,7 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
 #pragma unroll
                 for (int x = 0; x < 12; ++x)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[x][r] = 0.f;
+                    for (int r = 0; r < 4; ++r) acc[x][r] = kOzBias;
 #pragma unroll
                 for (int round = 0; round < 4; ++round)
 #pragma unroll
@@ -320,14 +341,18 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
                     }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    long long vh = 0, vl = 0;
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) vh = vh * 256 + oz_int(acc[d][r]);
-#pragma unroll
-                    for (int d = 0; d < 4; ++d)
-                        vl = vl * 256 + (oz_int(acc[4 + 2 * d][r]) + oz_int(acc[5 + 2 * d][r]));
-                    shi[r] = vh;
-                    slo[r] = vl;
+                    // 32-bit inner sums, then one 64-bit shift-add per partial
+                    // sum: an accumulator holds at most 4 * 16 * 255^2 =
+                    // 4,161,600 in magnitude, a two-accumulator sum 8,323,200,
+                    // and 257 times that is below 2^31
+                    const int h01 = oz_unbias(acc[0][r]) * 256 + oz_unbias(acc[1][r]);
+                    const int h23 = oz_unbias(acc[2][r]) * 256 + oz_unbias(acc[3][r]);
+                    const int l01 = (oz_unbias(acc[4][r]) + oz_unbias(acc[5][r])) * 256 +
+                                    (oz_unbias(acc[6][r]) + oz_unbias(acc[7][r]));
+                    const int l23 = (oz_unbias(acc[8][r]) + oz_unbias(acc[9][r])) * 256 +
+                                    (oz_unbias(acc[10][r]) + oz_unbias(acc[11][r]));
+                    shi[r] = (long long)h01 * 65536 + h23;
+                    slo[r] = (long long)l01 * 65536 + l23;
                 }
             }
             // outputs: rows gq (r = 0, 1) and gq + 8 (r = 2, 3), columns
@@ -349,7 +374,7 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
                 double* c = Cp + i + (long long)g.ldc * j;
                 if constexpr (EM == 0) *c = v;
                 else if constexpr (EM == 1) *c = alpha * v;
-                else *c = beta_zero ? alpha * v : fma(beta, *c, alpha * v);
+                else *c = beta_zero ? alpha * v : fma(beta, cold[r], alpha * v);
             }
         }
     }

@@ -39,8 +39,9 @@
 namespace sbg {
 
 // shared-memory slots per lane and stage of the complex kernel: 8 entries of
-// op(A) and 8 of op(B), 16 bytes each
-constexpr int kZSlots = 16;
+// op(A), 8 of op(B) and (general epilogue) the 8 old C entries of the lane's
+// outputs, 16 bytes each
+constexpr int kZSlots = 24;
 inline constexpr size_t oz_z_smem_bytes(int threads) {
     return (size_t)(threads / 32) * 2 * kZSlots * 32 * sizeof(double2);
 }
@@ -62,7 +63,8 @@ struct OzZArgs {
 // One real digit-split product of the warp's 16 x 16 x 8 block: the 36 MMAs
 // of the digit pairs s + t <= 7 into 12 accumulators (diagonals 0..3 one
 // each, 4..7 two each: no accumulator sums more than four products), read
-// back as integers and added to (neg: subtracted from) the two partial sums
+// back as integers (the accumulators start at kOzBias) and added to (neg:
+// subtracted from) the two partial sums
 // hi = sum_{d<4} 256^(3-d) D_d and lo = sum_{d>=4} 256^(7-d) D_d of every
 // output r of the lane.
 __device__ __forceinline__ void oz_product(const unsigned (&fa)[8][4], const unsigned (&fb)[8][2],
@@ -71,7 +73,7 @@ __device__ __forceinline__ void oz_product(const unsigned (&fa)[8][4], const uns
 #pragma unroll
     for (int x = 0; x < 12; ++x)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[x][r] = 0.f;
+        for (int r = 0; r < 4; ++r) acc[x][r] = kOzBias;
 #pragma unroll
     for (int round = 0; round < 4; ++round)
 #pragma unroll
@@ -90,12 +92,12 @@ __device__ __forceinline__ void oz_product(const unsigned (&fa)[8][4], const uns
         // 32-bit inner sums, then one 64-bit shift-add per partial sum: an
         // accumulator holds at most 4 * 16 * 255^2 = 4,161,600 in magnitude,
         // a two-accumulator sum 8,323,200, and 257 times that is below 2^31
-        const int h01 = oz_int(acc[0][r]) * 256 + oz_int(acc[1][r]);
-        const int h23 = oz_int(acc[2][r]) * 256 + oz_int(acc[3][r]);
-        const int l01 = (oz_int(acc[4][r]) + oz_int(acc[5][r])) * 256 +
-                        (oz_int(acc[6][r]) + oz_int(acc[7][r]));
-        const int l23 = (oz_int(acc[8][r]) + oz_int(acc[9][r])) * 256 +
-                        (oz_int(acc[10][r]) + oz_int(acc[11][r]));
+        const int h01 = oz_unbias(acc[0][r]) * 256 + oz_unbias(acc[1][r]);
+        const int h23 = oz_unbias(acc[2][r]) * 256 + oz_unbias(acc[3][r]);
+        const int l01 = (oz_unbias(acc[4][r]) + oz_unbias(acc[5][r])) * 256 +
+                        (oz_unbias(acc[6][r]) + oz_unbias(acc[7][r]));
+        const int l23 = (oz_unbias(acc[8][r]) + oz_unbias(acc[9][r])) * 256 +
+                        (oz_unbias(acc[10][r]) + oz_unbias(acc[11][r]));
         const long long vh = (long long)h01 * 65536 + h23;
         const long long vl = (long long)l01 * 65536 + l23;
         hi[r] += neg ? -vh : vh;
@@ -181,9 +183,10 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
     // Operands of the warp's next pair are prefetched into shared memory
     // (two stages per warp, 16-byte cp.async with zero fill outside the
     // shape) while the current pair computes: slot e of lane L at
-    // stage * kZSlots * 32 + e * 32 + L holds the lane's A entry e (e < 8) or
-    // B entry e - 8 (column half (e - 8) / 4); consecutive lanes read
-    // consecutive 16-byte words.
+    // stage * kZSlots * 32 + e * 32 + L holds the lane's A entry e (e < 8), B
+    // entry e - 8 (column half (e - 8) / 4) or, when the epilogue reads C, the
+    // old C of output e - 16 (column half (e - 16) / 4); consecutive lanes
+    // read consecutive 16-byte words.
     extern __shared__ __align__(16) unsigned char oz_smem[];
     double2* wbuf = reinterpret_cast<double2*>(oz_smem) + (threadIdx.x >> 5) * (2 * kZSlots * 32);
     auto prefetch = [&](long long p, int stage) {
@@ -203,6 +206,17 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
             const bool in = l < k && j < n;
             const double2* src = g.tb ? Bp + j + (long long)g.ldb * l : Bp + l + (long long)g.ldb * j;
             cp_async16(d + (8 + e) * 32, in ? src : Bp, in ? 16 : 0);
+        }
+        if constexpr (EM == 2) {
+            if (!beta_zero) {                 // the old C of the lane's outputs
+                const double2* Cq = g.C + p * g.ldc2;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int i = gq + 8 * ((e >> 1) & 1), j = 2 * tq + (e & 1) + 8 * (e >> 2);
+                    const bool in = i < m && j < n;
+                    cp_async16(d + (16 + e) * 32, in ? Cq + i + (long long)g.ldc * j : Cq, in ? 16 : 0);
+                }
+            }
         }
     };
 
@@ -354,7 +368,7 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
                     w.y = fma(alpha.x, v.y, alpha.y * v.x);
                     if constexpr (EM == 2) {
                         if (!beta_zero) {             // + beta C
-                            const double2 c0 = *c;
+                            const double2 c0 = sl[(16 + 4 * h + r) * 32];
                             w.x = fma(beta.x, c0.x, fma(-beta.y, c0.y, w.x));
                             w.y = fma(beta.x, c0.y, fma(beta.y, c0.x, w.y));
                         }
