@@ -364,42 +364,42 @@ int variants_for(int type, int m, int n, int k) {
 //   complex64 at N = 1e5 and 1e6, and 5% less for fp32 at N = 1e5 (up to 20%
 //   per size), while fp32 at N = 1e6 measured the same total;
 // - the tensor-core kernel (digit-split products) for real fp64 at
-//   m = n = k = 15, 16, at 13, 14 with beta == 0, and at 16 x 8 x 16: with
-//   alpha = 1.5 at N = 1e5 it took 421 / 427 / 426 / 398 us for
-//   m = 13 / 14 / 15 / 16 against 496 / 508 / 648 / 739 us on the fp64 FMA
-//   pipe with beta = 0 (1.18-1.86x), 571 / 588 / 589 / 509 us against
-//   551 / 557 / 733 / 791 us with beta = -0.5 (C read and updated in fp64),
-//   and 289 us against 404 us for 16 x 8 x 16 (op(A) = T, beta = 1); below
-//   m = 13 and on the other FEM shapes the FMA kernels win, as the
+//   m = n = k = 13..16, at 12 with beta != 0, and at 16 x 8 x 16: with
+//   alpha = 1.5 at N = 1e5 it took 387 / 388 / 383 / 355 us for
+//   m = 13 / 14 / 15 / 16 against 494 / 508 / 647 / 738 us on the fp64 FMA
+//   pipe with beta = 0 (1.28-2.08x), 413 / 416 / 413 / 383 us against
+//   550 / 557 / 733 / 791 us with beta = -0.5 (1.33-2.06x), 416 against
+//   434 us at m = 12 with beta != 0 (385 against 333 with beta = 0), and
+//   236 us against 403 us for 16 x 8 x 16 (op(A) = T, beta = 1); below
+//   m = 12 and on the other FEM shapes the FMA kernels win, as the
 //   tensor-core kernel always computes a 16 x 16 x 16 product;
 // - for real fp64 shapes without specialised kernels, the tensor-core
-//   kernel (public variant 1) when m n k >= 1320 with beta == 0 or >= 1792
+//   kernel (public variant 1) when m n k >= 1024 with beta == 0 or >= 1320
 //   otherwise: over the 334 such shapes with m, n, k in {4, 8, 11, 13, 14,
-//   15, 16}, op N/N, N = 1e5, this rule took 101.4 / 123.7 ms in total
-//   (beta == 0 / beta = -0.5) against 100.6 / 121.0 ms for the best
-//   variant of each shape and 129.5 / 135.3 ms for the generic kernel alone;
-// - the tensor-core kernel for complex128 at m = n = k = 13..16, at 12 with
-//   beta == 0, and at 16 x 8 x 16: with alpha = 1.5 at N = 1e5 it took
-//   1.21 / 1.22 / 1.23 / 1.20 ms for m = 13 / 14 / 15 / 16 against 1.95 /
-//   2.25 / 2.49 / 2.87 ms on the fp64 FMA pipe with beta = 0 (1.6-2.4x;
-//   1.35-2.2x with beta = -0.5), 1.20 against 1.28 ms at m = 12 (even with
-//   beta != 0), and 0.80 against 1.88 ms for 16 x 8 x 16 (op(A) = T,
-//   beta = 1); on the complex128 shapes without specialised kernels, the
-//   tensor-core kernel (public variant 1) when m n k >= 1144 (beta == 0) or
-//   1232: over the 334 such shapes of the fp64 rule's grid, op N/N, N = 1e5,
-//   289.8 / 336.9 ms in total against 288.4 / 334.6 ms for the best variant
-//   of each and 412.2 / 452.9 ms for the generic kernel alone;
+//   15, 16}, op N/N, N = 1e5, this rule took 95.0 / 101.7 ms in total
+//   (beta == 0 / beta = -0.5) against 94.3 / 100.8 ms for the best variant
+//   of each shape and 129.6 / 135.3 ms for the generic kernel alone;
+// - the tensor-core kernel for complex128 at m = n = k = 12..16 and at
+//   16 x 8 x 16: with alpha = 1.5 at N = 1e5 it took 1.12 / 1.13 / 1.15 /
+//   1.16 / 1.12 ms for m = 12 / 13 / 14 / 15 / 16 against 1.28 / 1.95 /
+//   2.25 / 2.48 / 2.88 ms on the fp64 FMA pipe with beta = 0 (1.14-2.57x;
+//   1.09-2.35x with beta = -0.5), and 0.80 against 1.88 ms for 16 x 8 x 16
+//   (op(A) = T, beta = 1); at m = 11 they were even; on the complex128
+//   shapes without specialised kernels, the tensor-core kernel (public
+//   variant 1) when m n k >= 1024: over the same 334 shapes, 277.1 / 316.4 ms
+//   in total against 275.6 / 314.9 ms for the best variant of each and
+//   411.4 / 452.0 ms for the generic kernel alone;
 // - variant 0 otherwise (fp64 and complex128, bound by the fp64 pipe, showed
 //   no difference; the 16-bit CUDA-core kernels were mixed).
 int default_variant(int type, int m, int n, int k, int bz, int sc) {
     if (type == SBGEMM_TYPE_Z) {
-        if (!has_specialized(0, m, n, k)) return m * n * k >= (bz ? 1144 : 1232) ? 1 : 0;
-        if (m == n && n == k && (m >= 13 || (m == 12 && bz))) return kMmaVariant;
+        if (!has_specialized(0, m, n, k)) return m * n * k >= 1024 ? 1 : 0;
+        if (m == n && n == k && m >= 12) return kMmaVariant;
         if (m == 16 && n == 8 && k == 16) return kMmaVariant;
     }
     if (type == SBGEMM_TYPE_D) {
-        if (!has_specialized(0, m, n, k)) return m * n * k >= (bz ? 1320 : 1792) ? 1 : 0;
-        if (m == n && n == k && (m >= 15 || (m >= 13 && bz))) return kMmaVariant;
+        if (!has_specialized(0, m, n, k)) return m * n * k >= (bz ? 1024 : 1320) ? 1 : 0;
+        if (m == n && n == k && (m >= 13 || (m == 12 && !bz))) return kMmaVariant;
         if (m == 16 && n == 8 && k == 16) return kMmaVariant;
     }
     if ((type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && has_mma_variant(type, m, n, k) &&

@@ -114,25 +114,29 @@ def test_variant_table_host_logic():
     assert sbgemm.get_choice("c", 10, 10, 10, 0, 0, 1, 6) == 2
     assert sbgemm.get_choice("d", 10, 10, 10, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 1, 5) == 7
-    # generic fp64 shapes: the tensor-core kernel (variant 1) from m n k = 1320
-    # (beta == 0) or 1792 (beta != 0)
+    # generic fp64 shapes: the tensor-core kernel (variant 1) from m n k = 1024
+    # (beta == 0) or 1320 (beta != 0)
     assert sbgemm.get_choice("d", 16, 16, 15, 0, 0, 1, 5) == 1
-    assert sbgemm.get_choice("d", 8, 11, 15, 0, 0, 1, 5) == 1
-    assert sbgemm.get_choice("d", 8, 11, 15, 0, 0, 0, 5) == 0
+    assert sbgemm.get_choice("d", 8, 8, 16, 0, 0, 1, 5) == 1
+    assert sbgemm.get_choice("d", 8, 8, 16, 0, 0, 0, 5) == 0
+    assert sbgemm.get_choice("d", 8, 11, 15, 0, 0, 0, 5) == 1
     assert sbgemm.get_choice("d", 7, 3, 11, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("s", 16, 16, 15, 0, 0, 1, 5) == 0
-    # complex128: the tensor cores at m = n = k >= 13, 12 with beta == 0, and
-    # 16 x 8 x 16
+    # complex128: the tensor cores at m = n = k >= 12 and 16 x 8 x 16, on
+    # generic shapes from m n k = 1024; real fp64 at m = n = k >= 13 and 12
+    # with beta != 0
     assert sbgemm.get_choice("z", 13, 13, 13, 0, 0, 0, 5) == 7
     assert sbgemm.get_choice("z", 12, 12, 12, 0, 0, 1, 5) == 7
-    assert sbgemm.get_choice("z", 12, 12, 12, 0, 0, 0, 5) == 0
+    assert sbgemm.get_choice("z", 12, 12, 12, 0, 0, 0, 5) == 7
     assert sbgemm.get_choice("z", 16, 8, 16, 1, 0, 0, 5) == 7
     assert sbgemm.get_choice("z", 11, 11, 11, 0, 0, 1, 5) == 0
     assert sbgemm.get_choice("z", 16, 16, 15, 0, 0, 1, 5) == 1
-    assert sbgemm.get_choice("z", 8, 11, 13, 0, 0, 1, 5) == 1
-    assert sbgemm.get_choice("z", 8, 11, 13, 0, 0, 0, 5) == 0
-    assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 0
+    assert sbgemm.get_choice("z", 8, 11, 13, 0, 0, 0, 5) == 1
+    assert sbgemm.get_choice("z", 8, 8, 15, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("d", 13, 13, 13, 1, 0, 0, 5) == 7
     assert sbgemm.get_choice("d", 12, 12, 12, 0, 0, 1, 5) == 0
+    assert sbgemm.get_choice("d", 12, 12, 12, 0, 0, 0, 5) == 7
+    assert sbgemm.get_choice("d", 11, 11, 11, 0, 0, 0, 5) == 0
     assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 7
     assert sbgemm.get_choice("h", 16, 16, 16, 0, 0, 1, 6) == 7
     assert sbgemm.get_choice("h", 12, 12, 12, 0, 0, 1, 6) == 0

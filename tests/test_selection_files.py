@@ -91,11 +91,13 @@ def test_selector_modes():
     assert L.sbgemm_default_variant(D, 10, 10, 10, 1, 5) == 0
     assert L.sbgemm_default_variant(S, 7, 3, 11, 1, 5) == 0
     assert L.sbgemm_default_variant(S, 17, 3, 11, 1, 5) == -1
-    # real fp64 on the tensor cores: m = n = k >= 15, 13 and 14 with beta == 0, 16 x 8 x 16
+    # real fp64 on the tensor cores: m = n = k >= 13, 12 with beta != 0, 16 x 8 x 16
     assert L.sbgemm_default_variant(D, 16, 16, 16, 0, 5) == 7
     assert L.sbgemm_default_variant(D, 13, 13, 13, 1, 5) == 7
-    assert L.sbgemm_default_variant(D, 13, 13, 13, 0, 5) == 0
+    assert L.sbgemm_default_variant(D, 13, 13, 13, 0, 5) == 7
+    assert L.sbgemm_default_variant(D, 12, 12, 12, 0, 5) == 7
     assert L.sbgemm_default_variant(D, 12, 12, 12, 1, 5) == 0
+    assert L.sbgemm_default_variant(D, 11, 11, 11, 0, 5) == 0
     assert L.sbgemm_default_variant(D, 16, 8, 16, 0, 6) == 7
     assert L.sbgemm_default_variant(D, 9, 16, 9, 0, 6) == 0
 
