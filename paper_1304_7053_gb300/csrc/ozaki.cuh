@@ -187,6 +187,20 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
     const long long warp = (blockIdx.x * (long long)NT + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * NT) >> 5;
     const int m = g.m, n = g.n, k = g.k;
+    if constexpr (EM == 2) {
+        // a device alpha of 0: C = beta C (0 when beta == 0), A and B unread
+        // (host scalars of 0 never reach this kernel)
+        if (alpha == 0.0) {
+            for (long long p = warp; p < g.batch; p += nwarps) {
+                double* Cp = g.C + p * g.ldc2;
+                for (int e = lane; e < m * n; e += 32) {
+                    double* c = Cp + e % m + (long long)g.ldc * (e / m);
+                    *c = beta_zero ? 0.0 : beta * *c;
+                }
+            }
+            return;
+        }
+    }
 
     // op(A)(i, l) and op(B)(l, j) of pair p, zero outside the shape
     auto ldA = [&](const double* Ap, int i, int l) -> double {

@@ -220,6 +220,26 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
         }
     };
 
+    if constexpr (EM == 2) {
+        // a device alpha of 0: C = beta C (0 when beta == 0), A and B unread
+        // (host scalars of 0 never reach this kernel)
+        if (alpha.x == 0.0 && alpha.y == 0.0) {
+            for (long long p = warp; p < g.batch; p += nwarps) {
+                double2* Cp = g.C + p * g.ldc2;
+                for (int e = lane; e < m * n; e += 32) {
+                    double2* c = Cp + e % m + (long long)g.ldc * (e / m);
+                    if (beta_zero) {
+                        *c = make_double2(0.0, 0.0);
+                    } else {
+                        const double2 c0 = *c;
+                        *c = make_double2(fma(beta.x, c0.x, -beta.y * c0.y),
+                                          fma(beta.x, c0.y, beta.y * c0.x));
+                    }
+                }
+            }
+            return;
+        }
+    }
     if (warp < g.batch) prefetch(warp, 0);
     cp_async_commit();
     int stage = 0;

@@ -99,10 +99,26 @@ def test_extreme_exponents_and_special_values():
     H.assert_parity(sub, g[fin].ravel().copy(), H.oracle_ref(sub, 1.0, 0.0), 1.0, 0.0)
 
 
-def test_device_scalars_and_default_selection():
-    b = inputs.UniformBatch("d", "N", "N", 16, 16, 16, 3001, seed=77)
-    got = H.run_gpu(b, 1.5, -0.5, variant=TC, device_scalars=True)
-    H.assert_parity(b, got, H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 12, 12), (16, 16, 15)])
+def test_device_scalars_and_default_selection(shape):
+    """alpha and beta read from device memory: the general case, a device
+    beta of 0 (C is not read: NaN-filled C), a device alpha of 0 (C = beta C,
+    A and B are not read: NaN-filled A), on the tensor-core variant (7, or 1
+    for a shape without specialised kernels) and on the default choice."""
+    m, n, k = shape
+    tc = TC if m == n == k else 1
+    b = inputs.UniformBatch("d", "N", "N", m, n, k, 3001, seed=77)
+    for variant in (tc, None):
+        got = H.run_gpu(b, 1.5, -0.5, variant=variant, device_scalars=True)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, -0.5), 1.5, -0.5)
+        C = b.C.copy(); C[:] = np.nan
+        got = H.run_gpu(b, 1.5, 0.0, variant=variant, device_scalars=True, C=C)
+        H.assert_parity(b, got, H.oracle_ref(b, 1.5, 0.0, C=C), 1.5, 0.0, C=C)
+        A = b.A.copy(); A[:] = np.nan
+        got = H.run_gpu(b, 0.0, -0.5, variant=variant, device_scalars=True, A=A)
+        H.assert_parity(b, got, H.oracle_ref(b, 0.0, -0.5, A=A), 0.0, -0.5, A=A)
+        got = H.run_gpu(b, 0.0, 0.0, variant=variant, device_scalars=True, A=A, C=C)
+        assert np.all(H.blocks(b, got) == 0.0)
 
 
 # shapes without specialised kernels: the tensor-core kernel is public

@@ -122,10 +122,25 @@ def test_extreme_exponents_and_special_values():
     H.assert_parity(sub, g[fin].ravel().copy(), H.oracle_ref(sub, 1.0 + 0j, 0j), 1.0 + 0j, 0j)
 
 
-def test_device_scalars():
-    b = inputs.UniformBatch("z", "C", "N", 16, 16, 16, 1501, seed=77)
-    got = H.run_gpu(b, ALPHA, BETAS[1], variant=TC, device_scalars=True)
-    H.assert_parity(b, got, H.oracle_ref(b, ALPHA, BETAS[1]), ALPHA, BETAS[1])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 12, 12), (16, 16, 15)])
+def test_device_scalars(shape):
+    """alpha and beta read from device memory: the general case, a device
+    beta of 0 (NaN-filled C is not read), a device alpha of 0 (C = beta C,
+    NaN-filled A is not read), on the tensor-core variant and the default."""
+    m, n, k = shape
+    tc = TC if m == n == k else 1
+    b = inputs.UniformBatch("z", "C", "N", m, n, k, 1501, seed=77)
+    for variant in (tc, None):
+        got = H.run_gpu(b, ALPHA, BETAS[1], variant=variant, device_scalars=True)
+        H.assert_parity(b, got, H.oracle_ref(b, ALPHA, BETAS[1]), ALPHA, BETAS[1])
+        C = b.C.copy(); C[:] = np.nan
+        got = H.run_gpu(b, ALPHA, 0j, variant=variant, device_scalars=True, C=C)
+        H.assert_parity(b, got, H.oracle_ref(b, ALPHA, 0j, C=C), ALPHA, 0j, C=C)
+        A = b.A.copy(); A[:] = np.nan
+        got = H.run_gpu(b, 0j, BETAS[1], variant=variant, device_scalars=True, A=A)
+        H.assert_parity(b, got, H.oracle_ref(b, 0j, BETAS[1], A=A), 0j, BETAS[1], A=A)
+        got = H.run_gpu(b, 0j, 0j, variant=variant, device_scalars=True, A=A, C=C)
+        assert np.all(H.blocks(b, got) == 0)
 
 
 GENERIC_SHAPES = [(16, 16, 15), (15, 16, 16), (14, 16, 12), (16, 9, 13), (13, 7, 16),
