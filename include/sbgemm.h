@@ -203,8 +203,10 @@ typedef struct {
  * call.  Groups that are square (m = n = k <= 16), op N/N, stored with
  * minimal leading dimensions and 16-byte aligned share ONE persistent
  * launch (up to 32 per launch): their tiles interleave, so small groups cost
- * no launch of their own.  Other groups run as separate uniform calls on the
- * same stream.  No group may read another group's C (they run
+ * no launch of their own.  Other groups, and fp64 / complex128 groups whose
+ * class the selector sends to the tensor-core variant (large sizes), run as
+ * separate uniform calls on the same stream.  No group may read another
+ * group's C (they run
  * concurrently).  Every group is checked before anything is queued; the
  * return value is that of the first failing check or launch.
  */

@@ -1,7 +1,9 @@
 // C entry point for several uniform batches in one call: qualifying groups
-// share one persistent launch (grouped.cuh), the rest run as separate
+// share one persistent launch (grouped.cuh), the rest (and the fp64 /
+// complex128 groups that take the tensor-core kernel) run as separate
 // uniform calls on the same stream.
 #include "grouped.cuh"
+#include "selection.h"
 
 namespace sbg {
 
@@ -112,6 +114,12 @@ extern "C" sbgemm_status sbgemm_gemm_grouped(int type, const void* alpha, const 
             const GKindInfo& k = kinfo[m - 1];
             fuse = k.ok && gtile_pairs(k, bz != 0, cfg) > 0;
         }
+        // fp64 and complex128 classes that the selector sends to the
+        // tensor-core kernel (large sizes: up to 2.1x / 2.6x the fp64 FMA
+        // pipe) run as their own uniform call, which takes that kernel
+        if (fuse && (type == SBGEMM_TYPE_D || type == SBGEMM_TYPE_Z) &&
+            select_variant(type, m, m, m, 0, 0, bz, size_class(G.batchCount)) == kMmaVariant)
+            fuse = false;
         if (fuse) {
             fused[nf++] = GIn{G.A, G.B, G.C, m, (long long)G.batchCount};
             if (nf == kGMaxGroups) {
