@@ -442,7 +442,12 @@ typedef struct sbgemm_vplan_s* sbgemm_vplan;
  * bucketed by (m, n, k, opA transposed, opB transposed), each bucket is cut
  * into tiles, and the tile list and per-problem records are uploaded to
  * device memory owned by the plan (allocated here, on the current device).
- * The C_q must not overlap.  Returns SBGEMM_ERR_INVALID_SIZE /
+ * For real and complex fp64, the buckets whose class the selector sends to
+ * the tensor-core kernel (as for a uniform batch of the bucket's size, beta
+ * taken as nonzero; large sizes under the built-in rule) are not tiled:
+ * their problems form a record list that the same run computes with that
+ * kernel, in a second launch.  The selection applies when the plan is
+ * built.  The C_q must not overlap.  Returns SBGEMM_ERR_INVALID_SIZE /
  * SBGEMM_ERR_INVALID_TRANS for a bad problem (nothing allocated).
  */
 sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,

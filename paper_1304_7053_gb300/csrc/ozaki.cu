@@ -1,6 +1,8 @@
 // Launchers of the fp64 tensor-core kernels (csrc/ozaki.cuh for real fp64,
 // csrc/ozaki_z.cuh for complex fp64): variant 7 of the shapes with
 // specialised kernels, variant 1 of the others.
+#include <cstring>
+
 #include "ozaki_z.cuh"
 
 namespace sbg {
@@ -43,6 +45,7 @@ sbgemm_status launch_oz(Kern kern, const Args& g, int NT, size_t smem, long long
 sbgemm_status run_ozaki_z(const Req& r) {
     constexpr int NT = 128;
     OzZArgs g;
+    g.recs = nullptr;
     g.A = static_cast<const double2*>(r.A);
     g.B = static_cast<const double2*>(r.B);
     g.C = static_cast<double2*>(r.C);
@@ -77,11 +80,77 @@ sbgemm_status run_ozaki_z(const Req& r) {
 
 }  // namespace
 
+static_assert(sizeof(OzRec) == 32, "OzRec mirrors the variable-size path's record layout");
+
+// The problems of a record list (element offsets from the arena bases A, B,
+// C; flags and shape per problem) on the tensor-core kernel of real or
+// complex fp64: the variable-size path's problems whose class takes it.
+sbgemm_status run_ozaki_records(int type, const void* recs, long long count, const void* A,
+                                const void* B, void* C, const void* alpha, const void* beta,
+                                int scalar_mode, int beta_zero, cudaStream_t stream) {
+    constexpr int NT = 128;
+    if (count <= 0) return SBGEMM_SUCCESS;
+    const bool dev = scalar_mode == SBGEMM_SCALARS_DEVICE;
+    if (type == SBGEMM_TYPE_D) {
+        OzArgs g;
+        std::memset(&g, 0, sizeof g);
+        g.recs = static_cast<const OzRec*>(recs);
+        g.A = static_cast<const double*>(A);
+        g.B = static_cast<const double*>(B);
+        g.C = static_cast<double*>(C);
+        g.batch = count;
+        if (dev) {
+            g.alpha_ptr = static_cast<const double*>(alpha);
+            g.beta_ptr = static_cast<const double*>(beta);
+        } else {
+            g.alpha = *static_cast<const double*>(alpha);
+            g.beta = *static_cast<const double*>(beta);
+            g.beta_zero = beta_zero;
+        }
+        // a host alpha of 0 takes the general epilogue, which scales C
+        const int em = dev || !beta_zero || g.alpha == 0.0 ? 2 : (g.alpha == 1.0 ? 0 : 1);
+        auto kern = em == 0 ? ozaki_kernel<NT, 0, true>
+                  : em == 1 ? ozaki_kernel<NT, 1, true> : ozaki_kernel<NT, 2, true>;
+        static thread_local OccCache occ[3];
+        return launch_oz(kern, g, NT, 0, count, occ[em], stream);
+    }
+    if (type == SBGEMM_TYPE_Z) {
+        OzZArgs g;
+        std::memset(&g, 0, sizeof g);
+        g.recs = static_cast<const OzRec*>(recs);
+        g.A = static_cast<const double2*>(A);
+        g.B = static_cast<const double2*>(B);
+        g.C = static_cast<double2*>(C);
+        g.batch = count;
+        if (dev) {
+            g.alpha_ptr = static_cast<const double2*>(alpha);
+            g.beta_ptr = static_cast<const double2*>(beta);
+        } else {
+            g.alpha = *static_cast<const double2*>(alpha);
+            g.beta = *static_cast<const double2*>(beta);
+            g.beta_zero = beta_zero;
+        }
+        const bool a0 = g.alpha.x == 0.0 && g.alpha.y == 0.0;
+        const bool a1 = g.alpha.x == 1.0 && g.alpha.y == 0.0;
+        const int em = dev || !beta_zero || a0 ? 2 : (a1 ? 0 : 1);
+        auto kern = em == 0 ? ozaki_z_kernel<NT, 0, true>
+                  : em == 1 ? ozaki_z_kernel<NT, 1, true> : ozaki_z_kernel<NT, 2, true>;
+        static thread_local OccCache occ[3];
+        static DeviceFlags attr[3];
+        const size_t smem = oz_z_smem_bytes(NT);
+        cudaError_t e = ensure_smem_limit(kern, (int)smem, attr[em]);
+        if (e != cudaSuccess) return (sbgemm_status)e;
+        return launch_oz(kern, g, NT, smem, count, occ[em], stream);
+    }
+    return SBGEMM_ERR_NOT_SUPPORTED;
+}
+
 sbgemm_status run_ozaki(const Req& r) {
     if (!ozaki_ok(r)) return SBGEMM_ERR_NOT_SUPPORTED;
     if (r.type == SBGEMM_TYPE_Z) return run_ozaki_z(r);
     constexpr int NT = 128;
     OzArgs g;
+    g.recs = nullptr;
     g.A = static_cast<const double*>(r.A);
     g.B = static_cast<const double*>(r.B);
     g.C = static_cast<double*>(r.C);

@@ -43,7 +43,18 @@
 
 namespace sbg {
 
+// One problem of a record list (the variable-size path): element offsets of
+// its A, B and C from the arena bases, flags (bits 0-1 op(A), 2-3 op(B):
+// 0 N, 1 T, 2 C; bit 4: C not read, as if beta were 0) and shape
+// (m | n << 8 | k << 16); matrices stored with minimal leading dimensions.
+struct OzRec {
+    long long a, b, c;
+    int flags;
+    int shape;
+};
+
 struct OzArgs {
+    const OzRec* recs;      // record list (REC kernels): g.batch records
     const double* A; const double* B; double* C;
     long long lda2, ldb2, ldc2;
     int lda, ldb, ldc;
@@ -174,7 +185,9 @@ __device__ __forceinline__ double oz_assemble(long long shi, long long slo, int 
 // EM: the epilogue, fixed per launch (a run-time select made the compiler
 // evaluate alpha * v for every entry on the slow fp64 pipe):
 // 0 C = v (alpha = 1, beta = 0), 1 C = alpha v (beta = 0), 2 the general case.
-template <int NT, int EM>
+// REC: the pairs are the problems of a record list (per-problem offsets,
+// shape, ops and beta flag) instead of a uniform 3-D batch.
+template <int NT, int EM, bool REC = false>
 __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
 {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
@@ -186,16 +199,33 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
     const int gq = lane >> 2, tq = lane & 3;
     const long long warp = (blockIdx.x * (long long)NT + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * NT) >> 5;
-    const int m = g.m, n = g.n, k = g.k;
+    // the current pair's shape, ops, leading dimensions and beta flag
+    int m = g.m, n = g.n, k = g.k;
+    int ta = g.ta, tb = g.tb, lda = g.lda, ldb = g.ldb, ldc = g.ldc;
+    bool bzp = beta_zero;                 // this pair's C is not read
+    auto pair = [&](long long p, const double*& Ap, const double*& Bp, double*& Cp) {
+        if constexpr (REC) {
+            const OzRec r = g.recs[p];
+            Ap = g.A + r.a; Bp = g.B + r.b; Cp = g.C + r.c;
+            m = r.shape & 255; n = (r.shape >> 8) & 255; k = (r.shape >> 16) & 255;
+            ta = (r.flags & 3) != 0; tb = ((r.flags >> 2) & 3) != 0;
+            lda = ta ? k : m; ldb = tb ? n : k; ldc = m;
+            bzp = beta_zero || (r.flags & 16) != 0;
+        } else {
+            Ap = g.A + p * g.lda2; Bp = g.B + p * g.ldb2; Cp = g.C + p * g.ldc2;
+        }
+    };
     if constexpr (EM == 2) {
-        // a device alpha of 0: C = beta C (0 when beta == 0), A and B unread
-        // (host scalars of 0 never reach this kernel)
+        // an alpha of 0 read from the device (or, for a record list, given
+        // on the host): C = beta C (0 when beta == 0), A and B unread
         if (alpha == 0.0) {
             for (long long p = warp; p < g.batch; p += nwarps) {
-                double* Cp = g.C + p * g.ldc2;
+                const double *Ap, *Bp;
+                double* Cp;
+                pair(p, Ap, Bp, Cp);
                 for (int e = lane; e < m * n; e += 32) {
-                    double* c = Cp + e % m + (long long)g.ldc * (e / m);
-                    *c = beta_zero ? 0.0 : beta * *c;
+                    double* c = Cp + e % m + (long long)ldc * (e / m);
+                    *c = bzp ? 0.0 : beta * *c;
                 }
             }
             return;
@@ -205,17 +235,17 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
     // op(A)(i, l) and op(B)(l, j) of pair p, zero outside the shape
     auto ldA = [&](const double* Ap, int i, int l) -> double {
         if (i >= m || l >= k) return 0.0;
-        return g.ta ? Ap[l + (long long)g.lda * i] : Ap[i + (long long)g.lda * l];
+        return ta ? Ap[l + (long long)lda * i] : Ap[i + (long long)lda * l];
     };
     auto ldB = [&](const double* Bp, int l, int j) -> double {
         if (l >= k || j >= n) return 0.0;
-        return g.tb ? Bp[j + (long long)g.ldb * l] : Bp[l + (long long)g.ldb * j];
+        return tb ? Bp[j + (long long)ldb * l] : Bp[l + (long long)ldb * j];
     };
 
     for (long long p = warp; p < g.batch; p += nwarps) {
-        const double* Ap = g.A + p * g.lda2;
-        const double* Bp = g.B + p * g.ldb2;
-        double* Cp = g.C + p * g.ldc2;
+        const double *Ap, *Bp;
+        double* Cp;
+        pair(p, Ap, Bp, Cp);
         // this lane's operand entries (the m16n8k16 fragment positions):
         // A rows gq, gq+8, columns 2tq, 2tq+1, 2tq+8, 2tq+9;
         // B rows 2tq, 2tq+1, 2tq+8, 2tq+9, columns gq (nh = 0), gq+8 (nh = 1)
@@ -294,11 +324,11 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
             // the load latency is hidden behind them (general epilogue only)
             double cold[4] = {0.0, 0.0, 0.0, 0.0};
             if constexpr (EM == 2) {
-                if (!beta_zero) {
+                if (!bzp) {
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const int i = gq + 8 * (r >> 1), j = 2 * tq + (r & 1) + 8 * h;
-                        if (i < m && j < n) cold[r] = Cp[i + (long long)g.ldc * j];
+                        if (i < m && j < n) cold[r] = Cp[i + (long long)ldc * j];
                     }
                 }
             }
@@ -385,10 +415,10 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
                     v = 0.0;
                     for (int l = 0; l < k; ++l) v = fma(ldA(Ap, i, l), ldB(Bp, l, j), v);
                 }
-                double* c = Cp + i + (long long)g.ldc * j;
+                double* c = Cp + i + (long long)ldc * j;
                 if constexpr (EM == 0) *c = v;
                 else if constexpr (EM == 1) *c = alpha * v;
-                else *c = beta_zero ? alpha * v : fma(beta, cold[r], alpha * v);
+                else *c = bzp ? alpha * v : fma(beta, cold[r], alpha * v);
             }
         }
     }

@@ -47,6 +47,7 @@ inline constexpr size_t oz_z_smem_bytes(int threads) {
 }
 
 struct OzZArgs {
+    const OzRec* recs;      // record list (REC kernels): g.batch records
     const double2* A; const double2* B; double2* C;
     long long lda2, ldb2, ldc2;
     int lda, ldb, ldc;
@@ -151,7 +152,9 @@ __device__ __forceinline__ int oz_expz(double2 z) {
 // EM: the epilogue, fixed per launch: 0 C = v (alpha = 1, beta = 0),
 // 1 C = alpha v (beta = 0), 2 the general case.  Two blocks per SM: the
 // fragments of both parts of op(A) and op(B) stay live (about 200 registers).
-template <int NT, int EM>
+// REC: the pairs are the problems of a record list (per-problem offsets,
+// shape, ops and beta flag) instead of a uniform 3-D batch.
+template <int NT, int EM, bool REC = false>
 __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
 {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
@@ -163,20 +166,46 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
     const int gq = lane >> 2, tq = lane & 3;
     const long long warp = (blockIdx.x * (long long)NT + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * NT) >> 5;
-    const int m = g.m, n = g.n, k = g.k;
+    // one pair's operands, shape, ops, leading dimensions and beta flag
+    struct Pair {
+        const double2* A; const double2* B; double2* C;
+        int m, n, k, ta, tb, ca, cb, lda, ldb, ldc;
+        bool bz;                              // C is not read
+    };
+    auto pair = [&](long long p) -> Pair {
+        Pair q;
+        if constexpr (REC) {
+            const OzRec r = g.recs[p];
+            q.A = g.A + r.a; q.B = g.B + r.b; q.C = g.C + r.c;
+            q.m = r.shape & 255; q.n = (r.shape >> 8) & 255; q.k = (r.shape >> 16) & 255;
+            const int oa = r.flags & 3, ob = (r.flags >> 2) & 3;
+            q.ta = oa != 0; q.tb = ob != 0; q.ca = oa == 2; q.cb = ob == 2;
+            q.lda = q.ta ? q.k : q.m; q.ldb = q.tb ? q.n : q.k; q.ldc = q.m;
+            q.bz = beta_zero || (r.flags & 16) != 0;
+        } else {
+            q.A = g.A + p * g.lda2; q.B = g.B + p * g.ldb2; q.C = g.C + p * g.ldc2;
+            q.m = g.m; q.n = g.n; q.k = g.k;
+            q.ta = g.ta; q.tb = g.tb; q.ca = g.ca; q.cb = g.cb;
+            q.lda = g.lda; q.ldb = g.ldb; q.ldc = g.ldc;
+            q.bz = beta_zero;
+        }
+        return q;
+    };
+    Pair cur;                                 // the pair being computed
+    cur.m = cur.n = cur.k = 0;
 
-    // op(A)(i, l) and op(B)(l, j) of pair p (conjugated for op = C), zero
-    // outside the shape
-    auto ldA = [&](const double2* Ap, int i, int l) -> double2 {
-        if (i >= m || l >= k) return make_double2(0.0, 0.0);
-        double2 v = g.ta ? Ap[l + (long long)g.lda * i] : Ap[i + (long long)g.lda * l];
-        if (g.ca) v.y = -v.y;
+    // op(A)(i, l) and op(B)(l, j) of the current pair (conjugated for op = C),
+    // zero outside the shape
+    auto ldA = [&](int i, int l) -> double2 {
+        if (i >= cur.m || l >= cur.k) return make_double2(0.0, 0.0);
+        double2 v = cur.ta ? cur.A[l + (long long)cur.lda * i] : cur.A[i + (long long)cur.lda * l];
+        if (cur.ca) v.y = -v.y;
         return v;
     };
-    auto ldB = [&](const double2* Bp, int l, int j) -> double2 {
-        if (l >= k || j >= n) return make_double2(0.0, 0.0);
-        double2 v = g.tb ? Bp[j + (long long)g.ldb * l] : Bp[l + (long long)g.ldb * j];
-        if (g.cb) v.y = -v.y;
+    auto ldB = [&](int l, int j) -> double2 {
+        if (l >= cur.k || j >= cur.n) return make_double2(0.0, 0.0);
+        double2 v = cur.tb ? cur.B[j + (long long)cur.ldb * l] : cur.B[l + (long long)cur.ldb * j];
+        if (cur.cb) v.y = -v.y;
         return v;
     };
 
@@ -190,45 +219,44 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
     extern __shared__ __align__(16) unsigned char oz_smem[];
     double2* wbuf = reinterpret_cast<double2*>(oz_smem) + (threadIdx.x >> 5) * (2 * kZSlots * 32);
     auto prefetch = [&](long long p, int stage) {
-        const double2* Ap = g.A + p * g.lda2;
-        const double2* Bp = g.B + p * g.ldb2;
+        const Pair q = pair(p);
         double2* d = wbuf + stage * kZSlots * 32 + lane;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int i = gq + 8 * ((e >> 1) & 1), l = 2 * tq + (e & 1) + 8 * (e >> 2);
-            const bool in = i < m && l < k;
-            const double2* src = g.ta ? Ap + l + (long long)g.lda * i : Ap + i + (long long)g.lda * l;
-            cp_async16(d + e * 32, in ? src : Ap, in ? 16 : 0);
+            const bool in = i < q.m && l < q.k;
+            const double2* src = q.ta ? q.A + l + (long long)q.lda * i : q.A + i + (long long)q.lda * l;
+            cp_async16(d + e * 32, in ? src : q.A, in ? 16 : 0);
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int l = 2 * tq + (e & 1) + 8 * ((e >> 1) & 1), j = gq + 8 * (e >> 2);
-            const bool in = l < k && j < n;
-            const double2* src = g.tb ? Bp + j + (long long)g.ldb * l : Bp + l + (long long)g.ldb * j;
-            cp_async16(d + (8 + e) * 32, in ? src : Bp, in ? 16 : 0);
+            const bool in = l < q.k && j < q.n;
+            const double2* src = q.tb ? q.B + j + (long long)q.ldb * l : q.B + l + (long long)q.ldb * j;
+            cp_async16(d + (8 + e) * 32, in ? src : q.B, in ? 16 : 0);
         }
         if constexpr (EM == 2) {
-            if (!beta_zero) {                 // the old C of the lane's outputs
-                const double2* Cq = g.C + p * g.ldc2;
+            if (!q.bz) {                      // the old C of the lane's outputs
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int i = gq + 8 * ((e >> 1) & 1), j = 2 * tq + (e & 1) + 8 * (e >> 2);
-                    const bool in = i < m && j < n;
-                    cp_async16(d + (16 + e) * 32, in ? Cq + i + (long long)g.ldc * j : Cq, in ? 16 : 0);
+                    const bool in = i < q.m && j < q.n;
+                    cp_async16(d + (16 + e) * 32, in ? q.C + i + (long long)q.ldc * j : q.C,
+                               in ? 16 : 0);
                 }
             }
         }
     };
 
     if constexpr (EM == 2) {
-        // a device alpha of 0: C = beta C (0 when beta == 0), A and B unread
-        // (host scalars of 0 never reach this kernel)
+        // an alpha of 0 read from the device (or, for a record list, given
+        // on the host): C = beta C (0 when beta == 0), A and B unread
         if (alpha.x == 0.0 && alpha.y == 0.0) {
             for (long long p = warp; p < g.batch; p += nwarps) {
-                double2* Cp = g.C + p * g.ldc2;
-                for (int e = lane; e < m * n; e += 32) {
-                    double2* c = Cp + e % m + (long long)g.ldc * (e / m);
-                    if (beta_zero) {
+                const Pair q = pair(p);
+                for (int e = lane; e < q.m * q.n; e += 32) {
+                    double2* c = q.C + e % q.m + (long long)q.ldc * (e / q.m);
+                    if (q.bz) {
                         *c = make_double2(0.0, 0.0);
                     } else {
                         const double2 c0 = *c;
@@ -244,9 +272,9 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
     cp_async_commit();
     int stage = 0;
     for (long long p = warp; p < g.batch; p += nwarps, stage ^= 1) {
-        const double2* Ap = g.A + p * g.lda2;
-        const double2* Bp = g.B + p * g.ldb2;
-        double2* Cp = g.C + p * g.ldc2;
+        cur = pair(p);
+        const int m = cur.m, n = cur.n, k = cur.k;
+        double2* Cp = cur.C;
         if (p + nwarps < g.batch) prefetch(p + nwarps, stage ^ 1);
         cp_async_commit();
         cp_async_wait_dyn(1);                 // this pair's operands have landed
@@ -258,13 +286,13 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             a[e] = sl[e * 32];
-            if (g.ca) a[e].y = -a[e].y;
+            if (cur.ca) a[e].y = -a[e].y;
         }
         auto loadB = [&](int h, double2 (&b)[4]) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 b[q] = sl[(8 + 4 * h + q) * 32];
-                if (g.cb) b[q].y = -b[q].y;
+                if (cur.cb) b[q].y = -b[q].y;
             }
         };
         // row and column exponents over both parts, reduced over the quad
@@ -372,14 +400,14 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
                     // fp64 FMAs for this entry (inputs out of the emulation's range)
                     v = make_double2(0.0, 0.0);
                     for (int l = 0; l < k; ++l) {
-                        const double2 x = ldA(Ap, i, l), y = ldB(Bp, l, j);
+                        const double2 x = ldA(i, l), y = ldB(l, j);
                         v.x = fma(x.x, y.x, v.x);
                         v.x = fma(-x.y, y.y, v.x);
                         v.y = fma(x.x, y.y, v.y);
                         v.y = fma(x.y, y.x, v.y);
                     }
                 }
-                double2* c = Cp + i + (long long)g.ldc * j;
+                double2* c = Cp + i + (long long)cur.ldc * j;
                 if constexpr (EM == 0) {
                     *c = v;
                 } else {
@@ -387,7 +415,7 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
                     w.x = fma(alpha.x, v.x, -alpha.y * v.y);
                     w.y = fma(alpha.x, v.y, alpha.y * v.x);
                     if constexpr (EM == 2) {
-                        if (!beta_zero) {             // + beta C
+                        if (!cur.bz) {                // + beta C
                             const double2 c0 = sl[(16 + 4 * h + r) * 32];
                             w.x = fma(beta.x, c0.x, fma(-beta.y, c0.y, w.x));
                             w.y = fma(beta.x, c0.y, fma(beta.y, c0.x, w.y));

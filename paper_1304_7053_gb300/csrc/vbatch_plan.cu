@@ -7,6 +7,7 @@
 #include <tuple>
 #include <vector>
 
+#include "selection.h"
 #include "vbatch.cuh"
 
 struct sbgemm_vplan_s {
@@ -19,6 +20,8 @@ struct sbgemm_vplan_s {
     sbg::VItem* items;
     sbg::VRec* recs;
     int* counter;
+    long long n_tc;        // problems on the fp64 / complex128 tensor-core kernel
+    sbg::VRec* tc_recs;    // their records (pad = m | n << 8 | k << 16)
 };
 
 namespace sbg {
@@ -29,6 +32,10 @@ namespace sbg {
                            void*, const void*, const void*, int, int, int, cudaStream_t);
 SBG_VDECL(S) SBG_VDECL(D) SBG_VDECL(C) SBG_VDECL(Z) SBG_VDECL(H) SBG_VDECL(B)
 #undef SBG_VDECL
+bool has_specialized(int type, int m, int n, int k);
+sbgemm_status run_ozaki_records(int type, const void* recs, long long count, const void* A,
+                                const void* B, void* C, const void* alpha, const void* beta,
+                                int scalar_mode, int beta_zero, cudaStream_t stream);
 
 namespace {
 
@@ -52,6 +59,16 @@ bool kinds_of(int type, VKindInfo* k) {
     case SBGEMM_TYPE_B: vkinds_B(k); return true;
     default: return false;
     }
+}
+
+// Real and complex fp64 problems whose class the selector sends to the
+// tensor-core kernel (large sizes; the table, the cost model or the
+// built-in rule as for a uniform batch of the bucket's size, beta taken
+// as nonzero) run on it, from a record list, instead of in the tiles.
+bool takes_tensor_cores(int type, int m, int n, int k, int ta, int tb, int count) {
+    if (type != SBGEMM_TYPE_D && type != SBGEMM_TYPE_Z) return false;
+    const int v = select_variant(type, m, n, k, ta, tb, 0, size_class(count));
+    return has_specialized(0, m, n, k) ? v == kMmaVariant : v == 1;
 }
 
 bool host_zero(int type, const void* p) {
@@ -108,7 +125,7 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
     const int kWindow = g_window;
     struct Tile { VItem it; double cost; };
     std::vector<Tile> tiles;
-    std::vector<VRec> recs;
+    std::vector<VRec> recs, tc_recs;
     recs.reserve(count);
     std::map<Key, int> all_keys;
     for (int w0 = 0; w0 < count; w0 += kWindow) {
@@ -126,6 +143,16 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
             int m, n, k, ta, tb;
             std::tie(m, n, k, ta, tb) = kv.first;
             const std::vector<int>& ids = kv.second;
+            if (takes_tensor_cores(type, m, n, k, ta, tb, (int)ids.size())) {
+                for (int q : ids) {
+                    const sbgemm_vproblem& p = problems[q];
+                    VRec r;
+                    r.a = p.a; r.b = p.b; r.c = p.c; r.flags = p.flags & 31;
+                    r.pad = m | (n << 8) | (k << 16);
+                    tc_recs.push_back(r);
+                }
+                continue;
+            }
             int kind = kVGeneric;
             if (m == n && n == k && !ta && !tb && kinfo[m - 1].mpr > 0) kind = m - 1;
             int T;
@@ -177,19 +204,26 @@ sbgemm_status sbgemm_vbatch_plan_create(sbgemm_vplan* plan, int type,
     const size_t recs_b = sizeof(VRec) * std::max<size_t>(1, recs.size());
     const size_t off_recs = (items_b + 255) / 256 * 256;
     const size_t off_ctr = off_recs + (recs_b + 255) / 256 * 256;
-    pl->bytes = off_ctr + 256;
+    const size_t off_tc = off_ctr + 256;
+    const size_t tc_b = sizeof(VRec) * std::max<size_t>(1, tc_recs.size());
+    pl->bytes = off_tc + (tc_b + 255) / 256 * 256;
+    pl->n_tc = (long long)tc_recs.size();
     cudaError_t e = cudaMalloc(&pl->dmem, pl->bytes);
     if (e != cudaSuccess) { delete pl; return (sbgemm_status)e; }
     char* base = static_cast<char*>(pl->dmem);
     pl->items = reinterpret_cast<VItem*>(base);
     pl->recs = reinterpret_cast<VRec*>(base + off_recs);
     pl->counter = reinterpret_cast<int*>(base + off_ctr);
+    pl->tc_recs = reinterpret_cast<VRec*>(base + off_tc);
     std::vector<VItem> hitems(tiles.size());
     for (size_t i = 0; i < tiles.size(); ++i) hitems[i] = tiles[i].it;
     if (!hitems.empty())
         e = cudaMemcpy(pl->items, hitems.data(), sizeof(VItem) * hitems.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !recs.empty())
         e = cudaMemcpy(pl->recs, recs.data(), sizeof(VRec) * recs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tc_recs.empty())
+        e = cudaMemcpy(pl->tc_recs, tc_recs.data(), sizeof(VRec) * tc_recs.size(),
+                       cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(pl->dmem); delete pl; return (sbgemm_status)e; }
     *plan = pl;
     return SBGEMM_SUCCESS;
@@ -218,7 +252,7 @@ sbgemm_status sbgemm_vbatch_run(sbgemm_vplan plan, const void* alpha, const void
     if (!plan) return SBGEMM_ERR_INVALID_VALUE;
     if (scalar_mode != SBGEMM_SCALARS_HOST && scalar_mode != SBGEMM_SCALARS_DEVICE)
         return SBGEMM_ERR_INVALID_VALUE;
-    if (plan->n_items == 0) return SBGEMM_SUCCESS;
+    if (plan->n_items == 0 && plan->n_tc == 0) return SBGEMM_SUCCESS;
     if (!alpha || !beta || !C) return SBGEMM_ERR_NULL_POINTER;
     int bz = 0, az = 0;
     if (scalar_mode == SBGEMM_SCALARS_HOST) {
@@ -227,6 +261,12 @@ sbgemm_status sbgemm_vbatch_run(sbgemm_vplan plan, const void* alpha, const void
     }
     if (!az && (!A || !B)) return SBGEMM_ERR_NULL_POINTER;
     cudaStream_t s = (cudaStream_t)stream;
+    if (plan->n_tc > 0) {
+        const sbgemm_status st = run_ozaki_records(plan->type, plan->tc_recs, plan->n_tc, A, B, C,
+                                                   alpha, beta, scalar_mode, bz, s);
+        if (st != SBGEMM_SUCCESS) return st;
+    }
+    if (plan->n_items == 0) return SBGEMM_SUCCESS;
 #define SBG_VRUN(T, CODE)                                                                      \
     case CODE:                                                                                 \
         return vrun_##T(plan->items, plan->n_items, plan->recs, plan->counter, A, B, C, alpha, \
