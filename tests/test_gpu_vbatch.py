@@ -155,8 +155,11 @@ def test_random_shapes_and_ops(dtype):
         check(dtype, desc, A, B, C, alpha, beta, got)
 
 
-@pytest.mark.parametrize("dtype", ["s", "z"])
+@pytest.mark.parametrize("dtype", ["s", "d", "z"])
 def test_graph_capture_and_device_scalars(dtype):
+    """Captured in a CUDA graph and replayed, and with device scalars; for
+    fp64 and complex128 the plan's tensor-core record list is a second
+    launch of the run."""
     desc, la, lb, lc = inputs.vbatch_problems(5000, seed=3)
     A, B, C = inputs.draw(dtype, la, 41), inputs.draw(dtype, lb, 42), inputs.draw(dtype, lc, 43)
     alpha, beta = (1.5 - 0.5j, -0.5 + 0.25j) if dtype in "cz" else (1.5, -0.5)
