@@ -7,10 +7,12 @@ precision, unit roundoff u = 2^-24 for fp32 arithmetic, 2^-53 for fp64):
   real:    |C - C_ref| <= max(2k, k + 3) u scale
   complex: |Re/Im (C - C_ref)| <= (2k + 5) u scale
 The k-term chain of FMAs contributes k roundings (2k per component for
-complex, whose real and imaginary parts are dot products of length 2k),
-alpha and the beta update add at most 3 more; max(2k, k+3) equals the
-literal 2ku for k >= 3 and covers k = 1, 2 where 2ku is below the k + 2
-roundings the evaluation can take.  16-bit storage adds the final rounding
+complex, whose real and imaginary parts are dot products of length 2k).
+Real epilogue: alpha * v (1 rounding), then fma(beta, C, .) (1), so at most
+k + 2 in all; max(2k, k+3) equals the literal 2ku for k >= 3 and covers
+k = 1, 2.  Complex epilogue, per component: alpha * v = fma(ar, vr, -ai vi)
+(2 roundings: the product ai vi and the fma), beta * C likewise (2), and the
+sum of the two (1): 2k + 5 in all, the bound used.  16-bit storage adds the final rounding
 of the fp32 result to the 16-bit format: u16 |C_ref| + (1 + u16) * bound32
 + s16, u16 = 2^-11 (binary16) or 2^-8 (bfloat16), s16 half the subnormal
 spacing (2^-25, 2^-134) for results below the normal range.
