@@ -8,7 +8,7 @@
 namespace sbg {
 
 bool ozaki_ok(const Req& r) {
-    return (r.type == SBGEMM_TYPE_D || r.type == SBGEMM_TYPE_Z) && !r.Cp && r.m >= 1 &&
+    return (r.type == SBGEMM_TYPE_D || r.type == SBGEMM_TYPE_Z) && r.m >= 1 &&
            r.n >= 1 && r.k >= 1;
 }
 
@@ -45,7 +45,7 @@ sbgemm_status launch_oz(Kern kern, const Args& g, int NT, size_t smem, long long
 sbgemm_status run_ozaki_z(const Req& r) {
     constexpr int NT = 128;
     OzZArgs g;
-    g.recs = nullptr;
+    std::memset(&g, 0, sizeof g);
     g.A = static_cast<const double2*>(r.A);
     g.B = static_cast<const double2*>(r.B);
     g.C = static_cast<double2*>(r.C);
@@ -68,14 +68,25 @@ sbgemm_status run_ozaki_z(const Req& r) {
     const bool alpha_one = g.alpha.x == 1.0 && g.alpha.y == 0.0;
     const int em = r.scalar_mode == SBGEMM_SCALARS_DEVICE ? 2
                  : !r.beta_zero ? 2 : (alpha_one ? 0 : 1);
-    static thread_local OccCache occ[3];
-    static DeviceFlags attr[3];
-    auto kern = em == 0 ? ozaki_z_kernel<NT, 0> : em == 1 ? ozaki_z_kernel<NT, 1>
-                                                         : ozaki_z_kernel<NT, 2>;
+    // per kernel instantiation: epilogue x (3-D layout, pointer arrays)
+    static thread_local OccCache occ[6];
+    static DeviceFlags attr[6];
+    // the pointer-array form reads pair p's matrices through the arrays
+    const bool ptrs = r.Cp != nullptr;
+    const int ki = em + (ptrs ? 3 : 0);
+    if (ptrs) {
+        g.Ap = reinterpret_cast<const double2* const*>(r.Ap);
+        g.Bp = reinterpret_cast<const double2* const*>(r.Bp);
+        g.Cp = reinterpret_cast<double2* const*>(r.Cp);
+    }
+    auto kern = ptrs ? (em == 0 ? ozaki_z_kernel<NT, 0, 2> : em == 1 ? ozaki_z_kernel<NT, 1, 2>
+                                                                     : ozaki_z_kernel<NT, 2, 2>)
+                     : (em == 0 ? ozaki_z_kernel<NT, 0> : em == 1 ? ozaki_z_kernel<NT, 1>
+                                                                  : ozaki_z_kernel<NT, 2>);
     const size_t smem = oz_z_smem_bytes(NT);
-    cudaError_t e = ensure_smem_limit(kern, (int)smem, attr[em]);
+    cudaError_t e = ensure_smem_limit(kern, (int)smem, attr[ki]);
     if (e != cudaSuccess) return (sbgemm_status)e;
-    return launch_oz(kern, g, NT, smem, r.batch, occ[em], r.stream);
+    return launch_oz(kern, g, NT, smem, r.batch, occ[ki], r.stream);
 }
 
 }  // namespace
@@ -109,8 +120,8 @@ sbgemm_status run_ozaki_records(int type, const void* recs, long long count, con
         }
         // a host alpha of 0 takes the general epilogue, which scales C
         const int em = dev || !beta_zero || g.alpha == 0.0 ? 2 : (g.alpha == 1.0 ? 0 : 1);
-        auto kern = em == 0 ? ozaki_kernel<NT, 0, true>
-                  : em == 1 ? ozaki_kernel<NT, 1, true> : ozaki_kernel<NT, 2, true>;
+        auto kern = em == 0 ? ozaki_kernel<NT, 0, 1>
+                  : em == 1 ? ozaki_kernel<NT, 1, 1> : ozaki_kernel<NT, 2, 1>;
         static thread_local OccCache occ[3];
         return launch_oz(kern, g, NT, 0, count, occ[em], stream);
     }
@@ -133,8 +144,8 @@ sbgemm_status run_ozaki_records(int type, const void* recs, long long count, con
         const bool a0 = g.alpha.x == 0.0 && g.alpha.y == 0.0;
         const bool a1 = g.alpha.x == 1.0 && g.alpha.y == 0.0;
         const int em = dev || !beta_zero || a0 ? 2 : (a1 ? 0 : 1);
-        auto kern = em == 0 ? ozaki_z_kernel<NT, 0, true>
-                  : em == 1 ? ozaki_z_kernel<NT, 1, true> : ozaki_z_kernel<NT, 2, true>;
+        auto kern = em == 0 ? ozaki_z_kernel<NT, 0, 1>
+                  : em == 1 ? ozaki_z_kernel<NT, 1, 1> : ozaki_z_kernel<NT, 2, 1>;
         static thread_local OccCache occ[3];
         static DeviceFlags attr[3];
         const size_t smem = oz_z_smem_bytes(NT);
@@ -150,7 +161,7 @@ sbgemm_status run_ozaki(const Req& r) {
     if (r.type == SBGEMM_TYPE_Z) return run_ozaki_z(r);
     constexpr int NT = 128;
     OzArgs g;
-    g.recs = nullptr;
+    std::memset(&g, 0, sizeof g);
     g.A = static_cast<const double*>(r.A);
     g.B = static_cast<const double*>(r.B);
     g.C = static_cast<double*>(r.C);
@@ -172,9 +183,18 @@ sbgemm_status run_ozaki(const Req& r) {
     // epilogue: C = v, C = alpha v, or the general form (device scalars)
     const int em = r.scalar_mode == SBGEMM_SCALARS_DEVICE ? 2
                  : !r.beta_zero ? 2 : (g.alpha == 1.0 ? 0 : 1);
-    auto kern = em == 0 ? ozaki_kernel<NT, 0> : em == 1 ? ozaki_kernel<NT, 1> : ozaki_kernel<NT, 2>;
-    static thread_local OccCache occ[3];
-    return launch_oz(kern, g, NT, 0, r.batch, occ[em], r.stream);
+    const bool ptrs = r.Cp != nullptr;
+    if (ptrs) {
+        g.Ap = reinterpret_cast<const double* const*>(r.Ap);
+        g.Bp = reinterpret_cast<const double* const*>(r.Bp);
+        g.Cp = reinterpret_cast<double* const*>(r.Cp);
+    }
+    auto kern = ptrs ? (em == 0 ? ozaki_kernel<NT, 0, 2> : em == 1 ? ozaki_kernel<NT, 1, 2>
+                                                                   : ozaki_kernel<NT, 2, 2>)
+                     : (em == 0 ? ozaki_kernel<NT, 0> : em == 1 ? ozaki_kernel<NT, 1>
+                                                                : ozaki_kernel<NT, 2>);
+    static thread_local OccCache occ[6];       // epilogue x (3-D layout, pointer arrays)
+    return launch_oz(kern, g, NT, 0, r.batch, occ[em + (ptrs ? 3 : 0)], r.stream);
 }
 
 }  // namespace sbg

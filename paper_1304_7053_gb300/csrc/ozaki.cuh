@@ -54,7 +54,9 @@ struct OzRec {
 };
 
 struct OzArgs {
-    const OzRec* recs;      // record list (REC kernels): g.batch records
+    const OzRec* recs;      // record list (source 1): g.batch records
+    const double* const* Ap; const double* const* Bp;   // pointer arrays (source 2)
+    double* const* Cp;
     const double* A; const double* B; double* C;
     long long lda2, ldb2, ldc2;
     int lda, ldb, ldc;
@@ -185,9 +187,10 @@ __device__ __forceinline__ double oz_assemble(long long shi, long long slo, int 
 // EM: the epilogue, fixed per launch (a run-time select made the compiler
 // evaluate alpha * v for every entry on the slow fp64 pipe):
 // 0 C = v (alpha = 1, beta = 0), 1 C = alpha v (beta = 0), 2 the general case.
-// REC: the pairs are the problems of a record list (per-problem offsets,
-// shape, ops and beta flag) instead of a uniform 3-D batch.
-template <int NT, int EM, bool REC = false>
+// SRC: where pair p's matrices are: 0 the uniform 3-D batch (base + p * ld2),
+// 1 a record list (per-problem offsets, shape, ops and beta flag), 2 device
+// arrays of per-pair pointers (the pointer-array form; uniform shape).
+template <int NT, int EM, int SRC = 0>
 __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
 {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
@@ -204,13 +207,15 @@ __global__ void __launch_bounds__(NT, 3) ozaki_kernel(OzArgs g)
     int ta = g.ta, tb = g.tb, lda = g.lda, ldb = g.ldb, ldc = g.ldc;
     bool bzp = beta_zero;                 // this pair's C is not read
     auto pair = [&](long long p, const double*& Ap, const double*& Bp, double*& Cp) {
-        if constexpr (REC) {
+        if constexpr (SRC == 1) {
             const OzRec r = g.recs[p];
             Ap = g.A + r.a; Bp = g.B + r.b; Cp = g.C + r.c;
             m = r.shape & 255; n = (r.shape >> 8) & 255; k = (r.shape >> 16) & 255;
             ta = (r.flags & 3) != 0; tb = ((r.flags >> 2) & 3) != 0;
             lda = ta ? k : m; ldb = tb ? n : k; ldc = m;
             bzp = beta_zero || (r.flags & 16) != 0;
+        } else if constexpr (SRC == 2) {
+            Ap = g.Ap[p]; Bp = g.Bp[p]; Cp = g.Cp[p];
         } else {
             Ap = g.A + p * g.lda2; Bp = g.B + p * g.ldb2; Cp = g.C + p * g.ldc2;
         }

@@ -47,7 +47,9 @@ inline constexpr size_t oz_z_smem_bytes(int threads) {
 }
 
 struct OzZArgs {
-    const OzRec* recs;      // record list (REC kernels): g.batch records
+    const OzRec* recs;      // record list (source 1): g.batch records
+    const double2* const* Ap; const double2* const* Bp;  // pointer arrays (source 2)
+    double2* const* Cp;
     const double2* A; const double2* B; double2* C;
     long long lda2, ldb2, ldc2;
     int lda, ldb, ldc;
@@ -152,9 +154,10 @@ __device__ __forceinline__ int oz_expz(double2 z) {
 // EM: the epilogue, fixed per launch: 0 C = v (alpha = 1, beta = 0),
 // 1 C = alpha v (beta = 0), 2 the general case.  Two blocks per SM: the
 // fragments of both parts of op(A) and op(B) stay live (about 200 registers).
-// REC: the pairs are the problems of a record list (per-problem offsets,
-// shape, ops and beta flag) instead of a uniform 3-D batch.
-template <int NT, int EM, bool REC = false>
+// SRC: where pair p's matrices are: 0 the uniform 3-D batch (base + p * ld2),
+// 1 a record list (per-problem offsets, shape, ops and beta flag), 2 device
+// arrays of per-pair pointers (the pointer-array form; uniform shape).
+template <int NT, int EM, int SRC = 0>
 __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
 {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
     };
     auto pair = [&](long long p) -> Pair {
         Pair q;
-        if constexpr (REC) {
+        if constexpr (SRC == 1) {
             const OzRec r = g.recs[p];
             q.A = g.A + r.a; q.B = g.B + r.b; q.C = g.C + r.c;
             q.m = r.shape & 255; q.n = (r.shape >> 8) & 255; q.k = (r.shape >> 16) & 255;
@@ -183,7 +186,11 @@ __global__ void __launch_bounds__(NT, 2) ozaki_z_kernel(OzZArgs g)
             q.lda = q.ta ? q.k : q.m; q.ldb = q.tb ? q.n : q.k; q.ldc = q.m;
             q.bz = beta_zero || (r.flags & 16) != 0;
         } else {
-            q.A = g.A + p * g.lda2; q.B = g.B + p * g.ldb2; q.C = g.C + p * g.ldc2;
+            if constexpr (SRC == 2) {
+                q.A = g.Ap[p]; q.B = g.Bp[p]; q.C = g.Cp[p];
+            } else {
+                q.A = g.A + p * g.lda2; q.B = g.B + p * g.ldb2; q.C = g.C + p * g.ldc2;
+            }
             q.m = g.m; q.n = g.n; q.k = g.k;
             q.ta = g.ta; q.tb = g.tb; q.ca = g.ca; q.cb = g.cb;
             q.lda = g.lda; q.ldb = g.ldb; q.ldc = g.ldc;

@@ -44,8 +44,8 @@ constexpr int kNumPipeVariants = 6;
 // Variant after the generic kernel: the tensor-core kernel of the 16-bit
 // types (csrc/mma16.cuh), for m = n = k = 8, 12 or 16, op N/N, flat layouts,
 // and of real and complex fp64 (csrc/ozaki.cuh, csrc/ozaki_z.cuh, any op
-// and layout of the uniform form); any other request given this variant
-// runs variant 0.
+// and layout of the uniform form, and the pointer-array form); any other
+// request given this variant runs variant 0.
 constexpr int kMmaVariant = kNumPipeVariants + 1;
 sbgemm_status run_mma16(const Req& r);   // mma16.cu
 bool mma16_ok(const Req& r);
