@@ -505,14 +505,17 @@ sbgemm_status sbgemm_vbatch_plan_info(sbgemm_vplan plan, int* n_tiles, int* n_bu
  *  - count above SBGEMM_NOALLOC_MAX_PROBLEMS returns SBGEMM_ERR_CAPACITY
  *    before anything is queued.
  *  - The first call on a device looks up the device address of the static
- *    array (set-up, once per device, with that device current); make that
- *    first call before any stream capture.
+ *    array (set-up, once per device, with that device current).
  *  - Every call uses the same array: it clears the counters it needs, but
  *    two calls whose work overlaps on the GPU (other streams, other host
  *    threads) race on it and give wrong results.
  *  - The tile count is read back to the host before the GEMM kernel is
  *    launched, so the call returns after the earlier work on `stream` and
- *    the bucketing kernels have finished.
+ *    the bucketing kernels have finished.  For the same reason this call
+ *    cannot be captured into a CUDA graph (use a plan and sbgemm_vbatch_run
+ *    for that).
+ *  - Every problem stays on the CUDA-core kernels (no tensor-core record
+ *    list as in a plan).
  *  - A problem with m, n or k outside 0..16, an op code of 3 or a negative
  *    offset gives SBGEMM_ERR_INVALID_SIZE (no GEMM is launched).
  */
