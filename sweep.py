@@ -445,6 +445,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--fp64tc-types", default="d,z", type=lambda v: v.split(","),
                     help="types of the fp64tc section (d, z)")
+    ap.add_argument("--fixed-types", default="s,d,c,z", type=lambda v: v.split(","),
+                    help="types of the fixed section")
     ap.add_argument("--quick", action="store_true", help="N = 1e5 only, fewer sizes")
     ap.add_argument("--sections", default="small,fixed,ops,fem,interface,shared_a,16bit",
                     help="comma-separated subset of the sections to run "
@@ -507,7 +509,7 @@ def main(argv=None):
             emit(r, "small")
     # fixed-size sweep, op N/N
     if "fixed" in want:
-        for dtype in ("s", "d", "c", "z"):
+        for dtype in args.fixed_types:
             for N in Ns:
                 for m in sizes:
                     for beta in (0.0, -0.5):
