@@ -310,7 +310,7 @@ sbgemm_status sbgemm_gemm_multi_uniform_variant(int type, char transa, char tran
  *   SBGEMM_SELECTOR_MODEL: the table's entry, else the installed cost
  *     model's choice, else the built-in rule.
  * Built-in rule: the tensor-core variant (7) for the 16-bit types at
- * m = n = k = 8 and 16, for real fp64 at m = n = k >= 13, at 12 with
+ * m = n = k = 8, 12 and 16, for real fp64 at m = n = k >= 13, at 12 with
  * beta != 0 and at 16 x 8 x 16, and for complex128 at m = n = k >= 12 and
  * at 16 x 8 x 16; on real and complex fp64 shapes without specialised
  * kernels the tensor-core variant (1) from m n k = 1024 (real fp64 with

@@ -11,7 +11,10 @@
 //           fragments loaded with ldmatrix (A^T with .trans).
 //   m = 12: as m = 16 with zero fragments for rows and columns 12..15; the
 //           fragments come from 32-bit and 16-bit shared loads (24-byte
-//           columns give no 16-byte rows for ldmatrix).
+//           columns give no 16-byte rows for ldmatrix) at per-lane offsets
+//           and masks fixed before the loop, so the loads are branch-free;
+//           each warp takes two pairs per iteration, their loads and MMAs
+//           issued before either pair's stores.
 //   m = 8:  two pairs per MMA, packed block-diagonally: A operand =
 //           diag(B0^T, B1^T) (16 x 16), B operand = [A0^T; A1^T] (16 x 8),
 //           result [C0^T; C1^T] (the off-diagonal fragment registers are 0).
@@ -170,25 +173,45 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
             // 12 x 12 pairs computed as 16 x 16 with zero fragments outside:
             // the 24-byte columns leave no 16-byte rows for ldmatrix, so the
             // fragments are read as 32-bit pairs (B^T rows are contiguous)
-            // and 16-bit entries (A^T: two columns of A per register)
-            for (int q = warp; q < cnt; q += 4) {
+            // and 16-bit entries (A^T: two columns of A per register).  Which
+            // fragment entries lie inside the matrix depends on the lane
+            // only: the offsets and masks are fixed per lane, invalid
+            // entries load from offset 0 and are masked (no branches), and
+            // two pairs are handled per iteration for independent loads.
+            const bool r1 = gq < 4;                    // row / column gq + 8 < 12
+            const bool c1 = tq < 2;                    // k index 2tq + 8 < 12
+            const int oB[4] = {2 * tq + 12 * gq, r1 ? 2 * tq + 12 * (gq + 8) : 0,
+                               c1 ? 2 * tq + 8 + 12 * gq : 0, (r1 && c1) ? 2 * tq + 8 + 12 * (gq + 8) : 0};
+            const unsigned mB[4] = {~0u, r1 ? ~0u : 0u, c1 ? ~0u : 0u, (r1 && c1) ? ~0u : 0u};
+            // A^T(l, i), A^T(l + 1, i) at As[i + 12 l], As[i + 12 (l + 1)] for
+            // (nt, kh): i = 8 nt + gq, l = 2tq + 8 kh
+            int oA[2][2];
+            unsigned mA[2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int kh = 0; kh < 2; ++kh) {
+                    const bool ok = (nt == 0 || r1) && (kh == 0 || c1);
+                    oA[nt][kh] = ok ? 8 * nt + gq + 12 * (2 * tq + 8 * kh) : 0;
+                    mA[nt][kh] = ok ? ~0u : 0u;
+                }
+            auto pair_product = [&](int q, float (&d)[2][4]) {
                 const unsigned short* Bs = reinterpret_cast<const unsigned short*>(st + P * slot + q * slot);
                 const unsigned short* As = reinterpret_cast<const unsigned short*>(st + q * slot);
-                auto fragB = [&](int j, int l) -> unsigned {          // B^T(j, l), B^T(j, l + 1)
-                    return (j < 12 && l < 12) ? *reinterpret_cast<const unsigned*>(Bs + l + 12 * j) : 0u;
-                };
-                auto fragA = [&](int i, int l) -> unsigned {          // A^T(l, i), A^T(l + 1, i)
-                    return (i < 12 && l < 12) ? (unsigned)As[i + 12 * l] | ((unsigned)As[i + 12 * (l + 1)] << 16)
-                                              : 0u;
-                };
-                float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-                if (!skip_ab) {
-                    const unsigned a[4] = {fragB(gq, 2 * tq), fragB(gq + 8, 2 * tq), fragB(gq, 2 * tq + 8),
-                                           fragB(gq + 8, 2 * tq + 8)};
+                unsigned a[4];
 #pragma unroll
-                    for (int nt = 0; nt < 2; ++nt)
-                        mma16816<Ty>(d[nt], a, fragA(8 * nt + gq, 2 * tq), fragA(8 * nt + gq, 2 * tq + 8));
-                }
+                for (int x = 0; x < 4; ++x) a[x] = *reinterpret_cast<const unsigned*>(Bs + oB[x]) & mB[x];
+                unsigned b[2][2];
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int kh = 0; kh < 2; ++kh)
+                        b[nt][kh] = ((unsigned)As[oA[nt][kh]] | ((unsigned)As[oA[nt][kh] + 12] << 16)) &
+                                    mA[nt][kh];
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) mma16816<Ty>(d[nt], a, b[nt][0], b[nt][1]);
+            };
+            auto pair_store = [&](int q, const float (&d)[2][4]) {
                 S* cp = gC + (p0 + q) * SE;
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
@@ -196,7 +219,7 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
 #pragma unroll
                     for (int hr = 0; hr < 2; ++hr) {
                         const int j = gq + 8 * hr;
-                        if (j >= 12) continue;
+                        if (hr == 1 && !r1) continue;        // j = 12..15
                         const int i = 8 * nt + 2 * tq;
                         float x = d[nt][2 * hr], y = d[nt][2 * hr + 1];
                         if (!alpha_one) { x *= alpha; y *= alpha; }
@@ -209,6 +232,17 @@ __global__ void __launch_bounds__(128) mma16_kernel(MmaArgs g)
                         *reinterpret_cast<unsigned*>(cp + i + 12 * j) = pack2<Ty>(x, y);
                     }
                 }
+            };
+            for (int q = warp; q < cnt; q += 8) {
+                const bool two = q + 4 < cnt;
+                float d0[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                float d1[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                if (!skip_ab) {
+                    pair_product(q, d0);
+                    if (two) pair_product(q + 4, d1);
+                }
+                pair_store(q, d0);
+                if (two) pair_store(q + 4, d1);
             }
         } else if constexpr (M == 16) {
             for (int q = warp; q < cnt; q += 4) {

@@ -355,9 +355,10 @@ int variants_for(int type, int m, int n, int k) {
 
 // The variant used without a table entry or cost model (sc: the batch's
 // size class, floor(log10 N)):
-// - the tensor-core kernel for the 16-bit types at m = n = k = 8 and 16
-//   (measured 1.3-1.7x faster; at m = 12 it measured slower than the
-//   CUDA-core kernel with beta = 0 and equal otherwise);
+// - the tensor-core kernel for the 16-bit types at m = n = k = 8, 12 and 16
+//   (measured 1.3-1.7x faster at 8 and 16; at m = 12, N = 1e6, binary16:
+//   178.8 against 197.2 us with beta = 0, 256.6 against 311.9 us with
+//   beta = -0.5);
 // - variant 2 (32 KB tiles, two stages: more blocks per SM and a shorter
 //   pipeline to fill) for complex64 and for fp32 below 1e6 pairs: over the
 //   square N/N sizes 2..16 it took 9% less total time than variant 0 for
@@ -402,8 +403,7 @@ int default_variant(int type, int m, int n, int k, int bz, int sc) {
         if (m == n && n == k && (m >= 13 || (m == 12 && !bz))) return kMmaVariant;
         if (m == 16 && n == 8 && k == 16) return kMmaVariant;
     }
-    if ((type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && has_mma_variant(type, m, n, k) &&
-        m != 12)
+    if ((type == SBGEMM_TYPE_H || type == SBGEMM_TYPE_B) && has_mma_variant(type, m, n, k))
         return kMmaVariant;
     if (!has_specialized(0, m, n, k)) return 0;
     if (type == SBGEMM_TYPE_C || (type == SBGEMM_TYPE_S && sc <= 5)) return 2;

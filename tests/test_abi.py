@@ -108,7 +108,7 @@ def test_variant_table_host_logic():
     sbgemm.clear_choices()
     # defaults without a table entry: 32 KB two-stage tiles (variant 2) for
     # fp32 below 1e6 pairs and for complex64, the tensor cores for 16-bit
-    # m = 8, 16, variant 0 elsewhere, the generic kernel (0) off the table
+    # m = 8, 12, 16, variant 0 elsewhere, the generic kernel (0) off the table
     assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 2
     assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 6) == 0
     assert sbgemm.get_choice("c", 10, 10, 10, 0, 0, 1, 6) == 2
@@ -139,7 +139,7 @@ def test_variant_table_host_logic():
     assert sbgemm.get_choice("d", 11, 11, 11, 0, 0, 0, 5) == 0
     assert sbgemm.get_choice("z", 16, 16, 16, 0, 0, 1, 5) == 7
     assert sbgemm.get_choice("h", 16, 16, 16, 0, 0, 1, 6) == 7
-    assert sbgemm.get_choice("h", 12, 12, 12, 0, 0, 1, 6) == 0
+    assert sbgemm.get_choice("h", 12, 12, 12, 0, 0, 1, 6) == 7
     assert sbgemm.get_choice("s", 7, 3, 11, 0, 0, 1, 5) == 0
     sbgemm.set_choice("s", 10, 10, 10, 0, 0, 1, 5, 3)
     assert sbgemm.get_choice("s", 10, 10, 10, 0, 0, 1, 5) == 3

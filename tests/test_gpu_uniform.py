@@ -244,7 +244,7 @@ def test_16bit_storage(dtype, m):
 @pytest.mark.parametrize("m", [8, 12, 16])
 def test_tensor_core_variant(dtype, m):
     """The mma.sync path of the 16-bit types (variant 7; the default for N/N
-    flat m = 8, 16)
+    flat m = 8, 12, 16)
     against the pipelined kernel's variant 0 and the oracle: ragged and tiny
     batches (odd counts leave m = 8 with a half-used MMA), beta zero and not,
     device scalars, and alpha = 0 with NaN in A and B (not read)."""
@@ -254,8 +254,7 @@ def test_tensor_core_variant(dtype, m):
             ref = H.oracle_ref(b, 1.5, beta)
             got7 = H.run_gpu(b, 1.5, beta, variant=7)
             H.assert_parity(b, got7, ref, 1.5, beta)
-            if m != 12:                              # the default there: the same kernel
-                assert np.array_equal(H.run_gpu(b, 1.5, beta), got7)
+            assert np.array_equal(H.run_gpu(b, 1.5, beta), got7)   # the default: same kernel
     b = inputs.UniformBatch(dtype, "N", "N", m, m, m, 777, seed=5)
     H.assert_parity(b, H.run_gpu(b, 1.5, -0.5, device_scalars=True), H.oracle_ref(b, 1.5, -0.5),
                     1.5, -0.5)

@@ -30,7 +30,7 @@ def clean_state():
 
 
 ENTRIES = [(S, 10, 10, 10, 0, 0, 1, 5, 4), (D, 16, 16, 16, 1, 0, 0, 6, 3),
-           (H, 12, 12, 12, 0, 0, 1, 6, 7), (C, 9, 16, 9, 1, 0, 0, 5, 6)]
+           (H, 12, 12, 12, 0, 0, 1, 6, 0), (C, 9, 16, 9, 1, 0, 0, 5, 6)]
 
 
 def test_table_file_round_trip(tmp_path):
@@ -84,7 +84,7 @@ def test_selector_modes():
     assert L.sbgemm_set_selector(7) == -5
     # the built-in rule itself
     assert L.sbgemm_default_variant(H, 16, 16, 16, 1, 6) == 7
-    assert L.sbgemm_default_variant(H, 12, 12, 12, 1, 6) == 0
+    assert L.sbgemm_default_variant(H, 12, 12, 12, 1, 6) == 7
     assert L.sbgemm_default_variant(C, 10, 10, 10, 1, 6) == 2
     assert L.sbgemm_default_variant(S, 10, 10, 10, 1, 5) == 2
     assert L.sbgemm_default_variant(S, 10, 10, 10, 1, 6) == 0
