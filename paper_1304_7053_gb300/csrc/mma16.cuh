@@ -327,10 +327,18 @@ sbgemm_status launch_mma16(const Req& r) {
         g.beta_zero = r.beta_zero;
     }
     const int per_pair = mma_slot_bytes(M) * (g.beta_zero ? 2 : 3);
-    int P = (24 * 1024) / per_pair;
+    // Stage bytes: 24 KB at m = 16 (three resident blocks of 128 threads);
+    // 14 KB at m = 8 and 12 (five blocks), where more resident warps hide the
+    // latency of the fragment loads.  Measured, binary16, N = 1e6, beta = 0 /
+    // beta != 0: m = 12 153.5 / 207.8 us against 177.2 / 254.2 us with 24 KB
+    // (stages of 10-20 KB: 150.7-180.6 / 207.8-235.9 us); m = 8 56.1 / 79.1
+    // against 57.7 / 80.0 us; m = 16 slower with any smaller stage.
+    constexpr int kStageBytes = (M == 16 ? 24 : 14) * 1024;
+    constexpr int kResident = M == 16 ? 3 : 5;
+    int P = kStageBytes / per_pair;
     P &= ~1;
     // at least two tiles per resident block when the batch is short
-    const long long want = 2LL * num_sms() * 3;
+    const long long want = 2LL * num_sms() * kResident;
     if ((r.batch + P - 1) / P < want) {
         long long p2 = (r.batch + want - 1) / want;
         p2 = (p2 + 1) & ~1LL;

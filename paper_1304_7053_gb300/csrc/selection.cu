@@ -357,7 +357,7 @@ int variants_for(int type, int m, int n, int k) {
 // size class, floor(log10 N)):
 // - the tensor-core kernel for the 16-bit types at m = n = k = 8, 12 and 16
 //   (measured 1.3-1.7x faster at 8 and 16; at m = 12, N = 1e6, binary16:
-//   178.8 against 197.2 us with beta = 0, 256.6 against 311.9 us with
+//   153.6 against 197.2 us with beta = 0, 207.8 against 311.9 us with
 //   beta = -0.5);
 // - variant 2 (32 KB tiles, two stages: more blocks per SM and a shorter
 //   pipeline to fill) for complex64 and for fp32 below 1e6 pairs: over the
