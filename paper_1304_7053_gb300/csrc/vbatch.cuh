@@ -7,8 +7,9 @@
 // size-specialised compute of the tile's bucket (the same register-blocked
 // code as the fixed-size path), and double-buffers the next tile's staging
 // behind the current tile's compute.  Each problem's matrices are contiguous
-// (minimal leading dimensions) at arbitrary arena offsets, so staging gathers
-// element-wise with asynchronous copies.
+// (minimal leading dimensions) at arbitrary arena offsets; staging copies
+// them asynchronously, in 16-byte chunks where the chunk boundaries of the
+// arena and of the matrix's slot line up (see the shifted slots below).
 #pragma once
 
 #include "sbgemm_launch.cuh"
@@ -99,6 +100,28 @@ __host__ __device__ constexpr int slot_quantum() {
                  16 / gcd_c(Cf::SC_P * Cf::ES, 16));
 }
 
+// Shifted slots.  A square kind whose matrices are not a whole number of
+// 16-byte chunks (odd sizes of the 4- and 8-byte types, and 16-bit sizes
+// that are not multiples of 8) and whose compute reads shared memory one
+// element at a time keeps each matrix in its slot at the element offset
+// that the matrix's global start has within its 16-byte chunk (its phase).
+// The chunk-aligned middle of every matrix then moves in 16-byte copies in
+// both directions, and only the ragged head and tail move element by
+// element.  In the packed arena of a variable-size batch most matrices start
+// off a 16-byte boundary, and these kinds could otherwise only copy
+// element by element.  A slot holds the matrix at any phase: its byte size
+// is the matrix's plus 16 - ES, rounded up to 16.
+template <class Cf>
+__host__ __device__ constexpr bool vshifted() {
+    return (Cf::SA * Cf::ES) % 16 != 0 && Cf::VL == 1 && Cf::VI == 1 && Cf::VJ == 1;
+}
+template <class Cf>
+__host__ __device__ constexpr int vslot_elems() {
+    return vshifted<Cf>() ? (Cf::SA * Cf::ES + 16 - Cf::ES + 15) / 16 * 16 / Cf::ES : Cf::SA_P;
+}
+template <class Cf>
+__host__ __device__ constexpr int vquantum() { return vshifted<Cf>() ? 1 : slot_quantum<Cf>(); }
+
 // Host view of a kind: matrices per compute round, staged bytes per pair
 // (A, B and old C slots), slot quantum.
 struct VKindInfo { int mpr; int bytes_per_pair; int quantum; };
@@ -107,7 +130,8 @@ template <class Ty, int s>
 constexpr VKindInfo vkind_info_one() {
     using K = VKindCfg<Ty, s>;
     using Cf = typename K::Cf;
-    return K::ok ? VKindInfo{Cf::MPR, (Cf::SA_P + Cf::SB_P + Cf::SC_P) * Cf::ES, slot_quantum<Cf>()}
+    static_assert(Cf::SA_P == Cf::SB_P && Cf::SB_P == Cf::SC_P, "square kinds share one slot size");
+    return K::ok ? VKindInfo{Cf::MPR, 3 * vslot_elems<Cf>() * Cf::ES, vquantum<Cf>()}
                  : VKindInfo{0, 0, 1};
 }
 
@@ -221,6 +245,144 @@ __device__ __forceinline__ void vstore_fixed(S* gC, const S* sC, const VRec* rec
     }
 }
 
+// Phase of a global address: its element offset within its 16-byte chunk
+// (addresses are aligned to the element size).
+template <class S>
+__device__ __forceinline__ int vphase(const S* p) {
+    return (int)((reinterpret_cast<uintptr_t>(p) & 15) / sizeof(S));
+}
+
+// A matrix of SE elements whose global start has phase h, in copy units:
+// nh head elements up to the first 16-byte boundary, nc 16-byte chunks,
+// nt tail elements.
+template <class S, int SE>
+struct VSplit {
+    int nh, nc, nt;
+    __device__ __forceinline__ explicit VSplit(int h) {
+        constexpr int EPC = 16 / sizeof(S);
+        nh = h ? min(EPC - h, SE) : 0;
+        nc = (SE - nh) / EPC;
+        nt = SE - nh - nc * EPC;
+    }
+};
+
+// Lanes per problem of the shifted copies: the chunk count of a matrix,
+// at least the ragged elements (at most 2 (16 / ES - 1)), at most a warp.
+template <class S, int SE>
+__host__ __device__ constexpr int vshift_lanes() {
+    constexpr int es = (int)sizeof(S);
+    constexpr int chunks = SE * es / 16, ragged = 2 * (16 / es - 1);
+    return (chunks > ragged ? chunks : ragged) >= 32 ? 32 : (chunks > ragged ? chunks : ragged);
+}
+
+// Copy one matrix into its shifted slot (dst = slot start + phase of src).
+// Lanes l0, l0 + LPP, ... take the 16-byte chunks (a loop of fixed trip
+// count, unrolled, predicated on the matrix's own chunk count); then lane
+// l0 < nh + nt takes one head or tail element.  dst + nh is 16-byte aligned
+// because the slot start is.
+template <class S, int SE, int LPP>
+__device__ __forceinline__ void vcopy_shifted(S* dst, const S* src, int l0) {
+    constexpr int ES = sizeof(S), EPC = 16 / ES;
+    constexpr int ITER = (SE / EPC + LPP - 1) / LPP;
+    const VSplit<S, SE> p(vphase(src));
+#pragma unroll
+    for (int i = 0; i < ITER; ++i) {
+        const int c = l0 + i * LPP;
+        if (c < p.nc) cp_async16(dst + p.nh + c * EPC, src + p.nh + c * EPC, 16);
+    }
+    if (l0 < p.nh + p.nt) {
+        const int e = l0 < p.nh ? l0 : l0 + p.nc * EPC;
+        vcopy_elem<S, ES>(dst + e, src + e);
+    }
+}
+
+// Stage the A, B (and old C) matrices of a tile of a shifted kind (slots of
+// SV elements), with the lane grouping of vstage_square.
+template <class S, int SE, int SV, int NT>
+__device__ __forceinline__ void vstage_shifted(S* sA, S* sB, S* sC, const VRec* rec, int cnt,
+                                               const S* gA, const S* gB, const S* gC, bool ab,
+                                               bool any_c) {
+    constexpr int LPP = vshift_lanes<S, SE>();
+    constexpr int PPW = 32 / LPP;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / LPP, l0 = lane - sub * LPP;
+    if (sub >= PPW) return;
+    for (int q = warp * PPW + sub; q < cnt; q += NW * PPW) {
+        const VRec r = rec[q];
+        if (ab) {
+            const S* a = gA + r.a;
+            const S* b = gB + r.b;
+            vcopy_shifted<S, SE, LPP>(sA + q * SV + vphase(a), a, l0);
+            vcopy_shifted<S, SE, LPP>(sB + q * SV + vphase(b), b, l0);
+        }
+        if (any_c && !(r.flags & 16)) {
+            const S* c = gC + r.c;
+            vcopy_shifted<S, SE, LPP>(sC + q * SV + vphase(c), c, l0);
+        }
+    }
+}
+
+// Write the shifted C slots of a tile back to each problem's C: 16-byte
+// stores for the chunk-aligned middle, element stores for head and tail
+// (the lane mapping of vcopy_shifted).
+template <class S, int SE, int SV, int NT>
+__device__ __forceinline__ void vstore_shifted(S* gC, const S* sC, const VRec* rec, int cnt) {
+    constexpr int EPC = 16 / (int)sizeof(S);
+    constexpr int LPP = vshift_lanes<S, SE>();
+    constexpr int ITER = (SE / EPC + LPP - 1) / LPP;
+    constexpr int PPW = 32 / LPP;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / LPP, l0 = lane - sub * LPP;
+    if (sub >= PPW) return;
+    for (int q = warp * PPW + sub; q < cnt; q += NW * PPW) {
+        S* dst = gC + rec[q].c;
+        const int h = vphase(dst);
+        const S* src = sC + q * SV + h;
+        const VSplit<S, SE> p(h);
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            const int c = l0 + i * LPP;
+            if (c < p.nc)
+                *reinterpret_cast<uint4*>(dst + p.nh + c * EPC) =
+                    *reinterpret_cast<const uint4*>(src + p.nh + c * EPC);
+        }
+        if (l0 < p.nh + p.nt) {
+            const int e = l0 < p.nh ? l0 : l0 + p.nc * EPC;
+            dst[e] = src[e];
+        }
+    }
+}
+
+// Compute a tile of a shifted kind in place in its C slots: each matrix is
+// read at its slot start plus its phase (compute_block with per-matrix
+// pointers: q = 0 and both operand offsets switched off).
+template <class Cf>
+__device__ __forceinline__ void vcompute_shifted(const typename Cf::S* sA, const typename Cf::S* sB,
+                                                 typename Cf::S* sC, const VRec* rec, int cnt,
+                                                 const typename Cf::S* gA, const typename Cf::S* gB,
+                                                 const typename Cf::S* gC, typename Cf::A alpha,
+                                                 typename Cf::A beta, bool beta_zero,
+                                                 bool alpha_one, bool skip_ab) {
+    using R = typename Cf::R;
+    constexpr int SV = vslot_elems<Cf>();
+    const int tid = threadIdx.x;
+    const int ql = tid / Cf::TPM;
+    const int u = tid - ql * Cf::TPM;
+    const int ti = u % Cf::TI, tj = u / Cf::TI;
+    if (ql >= Cf::MPR) return;
+    for (int q = ql; q < cnt; q += Cf::MPR) {
+        const VRec r = rec[q];
+        const R ca = ((r.flags & 3) == 2) ? R(-1) : R(1);
+        const R cb = (((r.flags >> 2) & 3) == 2) ? R(-1) : R(1);
+        typename Cf::S* c = sC + q * SV + vphase(gC + r.c);
+        compute_block<Cf>(sA + q * SV + vphase(gA + r.a), sB + q * SV + vphase(gB + r.b), c, c,
+                          nullptr, false, 0, ti, tj, alpha, beta, beta_zero || (r.flags & 16),
+                          alpha_one, skip_ab, ca, cb, 3);
+    }
+}
+
 // Write the C slots of a tile back to each problem's C (one warp per problem).
 template <class S, int NT>
 __device__ __forceinline__ void vstore(S* gC, const S* sC, const VRec* rec, int cnt, int SC,
@@ -300,13 +462,20 @@ __device__ __forceinline__ void vstage_kind(int kind, typename Ty::S* st, const 
             if constexpr (K::ok) {
                 using Cf = typename K::Cf;
                 using S = typename Ty::S;
-                constexpr int Q = slot_quantum<Cf>();
-                const int P = (cnt + Q - 1) / Q * Q;
                 static_assert(Cf::SA == Cf::SB && Cf::SB == Cf::SC && Cf::SA_P == Cf::SC_P,
                               "square kinds share one slot size");
-                vstage_square<S, Cf::SA, Cf::SA_P, kVThreads>(
-                    st, st + P * Cf::SA_P, st + P * (Cf::SA_P + Cf::SB_P), rec, cnt, g.A_, g.B_,
-                    g.C_, !skip_ab, !all_bz);
+                if constexpr (vshifted<Cf>()) {
+                    constexpr int SV = vslot_elems<Cf>();
+                    vstage_shifted<S, Cf::SA, SV, kVThreads>(st, st + cnt * SV, st + 2 * cnt * SV,
+                                                             rec, cnt, g.A_, g.B_, g.C_, !skip_ab,
+                                                             !all_bz);
+                } else {
+                    constexpr int Q = slot_quantum<Cf>();
+                    const int P = (cnt + Q - 1) / Q * Q;
+                    vstage_square<S, Cf::SA, Cf::SA_P, kVThreads>(
+                        st, st + P * Cf::SA_P, st + P * (Cf::SA_P + Cf::SB_P), rec, cnt, g.A_,
+                        g.B_, g.C_, !skip_ab, !all_bz);
+                }
             }
             return;
         }
@@ -325,14 +494,23 @@ __device__ __forceinline__ void vcompute_store_kind(int kind, typename Ty::S* st
             using K = VKindCfg<Ty, s>;
             if constexpr (K::ok) {
                 using Cf = typename K::Cf;
-                constexpr int Q = slot_quantum<Cf>();
-                const int P = (cnt + Q - 1) / Q * Q;
                 // every entry of C has one owning thread, which reads its old
                 // value and writes the result in the same slot: C in place
-                typename Ty::S* sC = st + P * (Cf::SA_P + Cf::SB_P);
-                vcompute_kind<Cf>(st, rec, cnt, P, sC, alpha, beta, all_bz, alpha_one, skip_ab);
-                __syncthreads();
-                vstore_fixed<typename Ty::S, Cf::SC, Cf::SC_P, kVThreads>(g.C_, sC, rec, cnt);
+                if constexpr (vshifted<Cf>()) {
+                    constexpr int SV = vslot_elems<Cf>();
+                    typename Ty::S* sC = st + 2 * cnt * SV;
+                    vcompute_shifted<Cf>(st, st + cnt * SV, sC, rec, cnt, g.A_, g.B_, g.C_, alpha,
+                                         beta, all_bz, alpha_one, skip_ab);
+                    __syncthreads();
+                    vstore_shifted<typename Ty::S, Cf::SC, SV, kVThreads>(g.C_, sC, rec, cnt);
+                } else {
+                    constexpr int Q = slot_quantum<Cf>();
+                    const int P = (cnt + Q - 1) / Q * Q;
+                    typename Ty::S* sC = st + P * (Cf::SA_P + Cf::SB_P);
+                    vcompute_kind<Cf>(st, rec, cnt, P, sC, alpha, beta, all_bz, alpha_one, skip_ab);
+                    __syncthreads();
+                    vstore_fixed<typename Ty::S, Cf::SC, Cf::SC_P, kVThreads>(g.C_, sC, rec, cnt);
+                }
             }
             return;
         }
