@@ -220,3 +220,62 @@ def test_tuned_window_installed_and_exact():
         check("s", desc, Ai, Bi, Ci, 1.5, -0.5, got, exact=True)
     finally:
         sbgemm.lib().sbgemm_vbatch_config(0)
+
+
+ES = {"s": 4, "d": 8, "c": 8, "z": 16, "h": 2, "b": 2}
+
+
+def phased_problems(dtype, reps, seed):
+    """Square N/N problems of every size 1..16 with each matrix starting at
+    every element offset within a 16-byte chunk (its phase), in a shuffled
+    arena order with gaps between matrices; about half flagged beta = 0.
+    Returns (desc, lenA, lenB, lenC)."""
+    epc = 16 // ES[dtype]
+    cases = np.array([(m, ph) for m in range(1, 17) for ph in range(epc) for _ in range(reps)],
+                     dtype=np.int64)
+    order = np.argsort(inputs.splitmix64(seed, len(cases)), kind="stable")
+    cases = cases[order]
+    r = inputs.splitmix64(seed + 1, 3 * len(cases)).reshape(3, -1)
+    desc = np.zeros((len(cases), 8), dtype=np.int64)
+    desc[:, 0] = desc[:, 1] = desc[:, 2] = cases[:, 0]
+    desc[:, 3] = ((r[0] >> np.uint64(63)).astype(np.int64)) << 4
+    ends = [0, 0, 0]
+    for q, (m, ph) in enumerate(cases):
+        for a in range(3):
+            # the operand a starts at the next offset of phase ph (operand b,
+            # c at phases shifted by the problem's own draw)
+            want = (ph + a * int(r[1 + (a > 1), q] % np.uint64(epc))) % epc
+            o = ends[a] + (want - ends[a]) % epc
+            desc[q, 4 + a] = o
+            ends[a] = o + m * m
+    return desc, ends[0] + epc, ends[1] + epc, ends[2] + epc
+
+
+@pytest.mark.parametrize("dtype", ["s", "d", "c", "z", "h", "b"])
+def test_every_phase_every_square_kind(dtype):
+    """Matrices at every 16-byte phase for every square size: the kinds that
+    keep matrices in shifted slots (odd sizes of the 4- and 8-byte types,
+    some 16-bit sizes) copy their middles in 16-byte chunks and their ragged
+    heads and tails element by element.  Results against the oracle (exact
+    on small integers for the 32- and 64-bit types), and the gaps of C
+    between problems keep their values (the oracle leaves them as given)."""
+    desc, la, lb, lc = phased_problems(dtype, 9, seed=91)
+    Ai, Bi, Ci = (inputs.draw(dtype, n, s, int_valued=True) for n, s in ((la, 92), (lb, 93), (lc, 94)))
+    cplx = dtype in "cz"
+    for alpha, beta in (((1.5 - 0.5j, -0.5 + 0.25j) if cplx else (1.5, -0.5)),
+                        ((0j, -0.5 + 0.25j) if cplx else (0.0, -0.5))):
+        got, info = run_vbatch(dtype, desc, Ai, Bi, Ci, alpha, beta)
+        assert info["buckets"] == 16
+        if dtype in "hb":
+            ref = oracle.gemm_vbatch(dtype, desc, alpha, Ai, Bi, beta, Ci, threads=8)
+            g = H.decode(got, dtype)
+            bd = (H.U16[dtype] * np.abs(ref) + (1 + H.U16[dtype]) *
+                  vbound(dtype, desc, Ai, Bi, Ci, alpha, beta) + H.SUB16[dtype])
+            assert np.all(np.abs(g - ref) <= bd)
+        else:
+            check(dtype, desc, Ai, Bi, Ci, alpha, beta, got, exact=True)
+    covered = np.zeros(lc, dtype=bool)
+    for q in range(desc.shape[0]):
+        covered[desc[q, 6]:desc[q, 6] + desc[q, 0] ** 2] = True
+    assert np.array_equal(got.view(np.uint8).reshape(lc, -1)[~covered],
+                          Ci.view(np.uint8).reshape(lc, -1)[~covered])
