@@ -474,7 +474,13 @@ sbgemm_status sbgemm_vbatch_config(int window);
  * the whole batch is a memset plus one kernel on `stream` and can be
  * captured into a CUDA graph.  alpha/beta as for the uniform entry points
  * (scalar_mode; fp32 scalars for the 16-bit types).  A, B, C are the
- * arenas.  Concurrent runs of the same plan race on its queue counter.
+ * arenas, each aligned to the element size (16 bytes for complex double).
+ * A matrix is moved in 16-byte chunks wherever its start and its size
+ * allow; for sizes whose matrices are not a whole number of 16-byte chunks
+ * (odd sizes of the 4- and 8-byte types, for example), the middle of the
+ * matrix moves in chunks at any start address and only the ragged head and
+ * tail move element by element.  Concurrent runs of the same plan race on
+ * its queue counter.
  */
 sbgemm_status sbgemm_vbatch_run(sbgemm_vplan plan, const void* alpha, const void* A,
                                 const void* B, const void* beta, void* C,
